@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the explicit PDN impact step on GB300.
+
+A step is one explicit time step of the whole hot path (striker update,
+contact detection/projection, hex8 + damage, interface + cohesive law, CSR
+gather + lumped-mass update, reaction sum) on the 100x150x4.4 mm plate,
+128x192x16 hex8 (393,216 elements), 16 seeded quasi-isotropic plies with
+interfaces, FP32 element arithmetic, FP64 integration, 5.5 kg striker at
+3 m/s.  The default run is the workload's full 20,000 steps.
+
+value  = element-updates/s = n_hex * K / (device time of the K timed steps),
+         max over ranks; inputs already resident in HBM.
+e2e    = the same metric through the C ABI from host buffers: mesh upload and
+         set-up, the K steps, and the read-back of the force history and the
+         final nodal state, all inside the timed region.
+roofline = the hex8 kernel's algorithmic bytes per launch / its mean launch
+         time (CUDA events on the library's stream, measured over a window of
+         the same run right after the timed region) against the measured HBM
+         copy bandwidth.
+cpu_baseline = the FP64 oracle (oracle/) on a bounded sample of the same
+         workload on this host's cores.
+
+--impl reference times the oracle alone on the same workload (bounded sample)
+and prints its own line.  Multi-GPU: one process per GPU, each rank runs an
+independent replica (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "element-updates/sec and HBM-roofline fraction at stated peak-contact-force error"
+UNIT = "element-updates/s"
+F32_PEAK_TOL = 5e-3     # peak contact force vs the FP64 oracle, asserted by tests/test_gpu_parity.py
+F32_DISP_TOL = 1e-4
+
+
+def hex_alg_bytes(n_hex: int, n_nodes: int) -> int:
+    """Algorithmic bytes of one hex8 launch: per element the connectivity
+    (32 B), the ply id (1 B) and the Gauss-point history read and written
+    (2 x 8 points x 7 fields x 4 B = 448 B); per node the FP32 reference
+    coordinates and displacement (12 + 12 B), each read once."""
+    return n_hex * (32 + 1 + 448) + n_nodes * 24
+
+
+def step_alg_bytes(n_hex, n_coh, n_nodes, n_surf) -> int:
+    """Algorithmic bytes of one whole step (every datum moved once):
+    hexes as above; interface elements connectivity + 4 thresholds read and
+    written; nodes: X and FP32 mirror read, mirror written, FP64 d and v read
+    and written, mass, flag; surface nodes: FP64 reference position."""
+    return (n_hex * (32 + 1 + 448) + n_coh * (32 + 2 * 4 * 4)
+            + n_nodes * (12 + 12 + 12 + 48 + 48 + 8 + 1) + n_surf * 48)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_for(args):
+    import pdn_inputs as pi
+    return pi.damage_fp32_plate(seed=args.seed)
+
+
+def oracle_rate(w, seconds: float, max_steps: int, threads: int):
+    """Oracle element-updates/s on a bounded sample of the workload's steps."""
+    import oracle
+    M = oracle.model_for(w, n_threads=threads)
+    M.step(1)  # first step outside the timing (thread pool start)
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps:
+        M.step(1)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    M.close()
+    return w.plate.n_hex * n / dt, n, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    w = workload_for(args)
+    cores = len(os.sched_getaffinity(0))
+    budget = max(10.0, min(120.0, args.ref_seconds))
+    # warm-up steps are part of the bounded sample's set-up
+    rate, n, dt = oracle_rate(w, budget, max(1, args.steps), cores)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_hex": w.plate.n_hex, "n_coh": w.plate.n_coh,
+                   "n_nodes": w.plate.n_nodes, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} of the workload's explicit steps from rest, FP64 oracle, {cores} threads"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2301_05552_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.lib()
+    w = workload_for(args)
+    plate = w.plate
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        solver = pkg.Solver(w, stream=stream.cuda_stream)
+    ctx = solver.ctx
+    K, W = args.steps, args.warmup
+    pkg.pdn_step(ctx, W)
+    rep0 = pkg.pdn_get_info(ctx)["n_repeats"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        pkg.pdn_step(ctx, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    info = pkg.pdn_get_info(ctx)
+    repeats = info["n_repeats"] - rep0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    kernels_per_pass = 5 if plate.n_coh > 0 else 4
+    gpu_launches = (K + repeats) * kernels_per_pass + 1  # + the target/mode kernel of the call
+    value = ws * plate.n_hex * K / (ms * 1e-3)
+
+    # per-kernel device times over a window of the same run (CUDA events on
+    # the library's stream around every launch)
+    prof = pkg.pdn_profile_kernels(ctx, args.profile_steps)
+    hex_ms = prof["hex"][0]
+    peak_gbs, peak_kind = measured_peaks()
+    alg = hex_alg_bytes(plate.n_hex, plate.n_nodes)
+    achieved = alg / (hex_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "hex_dram_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("kernel_source_hash") == kernel_source_hash() and tj.get("workload") == w.name:
+                traffic = tj["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    fh = pkg.pdn_contact_force(ctx)[2]
+    solver.close()
+
+    # end to end through the C ABI from host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        s2 = pkg.Solver(w, stream=stream.cuda_stream)
+        pkg.pdn_step(s2.ctx, K)
+        f_now, f_peak, hist = pkg.pdn_contact_force(s2.ctx)
+        d_fin, v_fin, imp = pkg.pdn_get_state(s2.ctx)
+    t_e2e = time.perf_counter() - t0
+    s2.close()
+    h2d = (plate.X.nbytes + plate.hex.nbytes + plate.coh.nbytes + plate.ply_of_hex.nbytes + plate.fixed.nbytes
+           + plate.surf.nbytes + plate.ply_angle_deg.nbytes)
+    d2h = hist.nbytes + d_fin.nbytes + v_fin.nbytes + 24 + 80
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e_value = ws * plate.n_hex * K / t_e2e
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": w.name, "n_hex": plate.n_hex, "n_coh": plate.n_coh, "n_nodes": plate.n_nodes,
+            "n_surf": plate.n_surf, "dt_s": info["dt"], "simulated_us": info["time"] * 1e6,
+            "precision": "FP32 element forces/damage/cohesive, FP64 integration, striker and gap test",
+            "l2": "inputs larger than L2 (working set %.0f MB)" % (info["device_bytes"] / 1e6),
+            "f_peak_N": float(fh.max()) if len(fh) else 0.0, "step_repeats": int(repeats),
+            "f_peak_rel_err_bound": F32_PEAK_TOL, "disp_rel_err_bound": F32_DISP_TOL,
+            "step_alg_bytes": step_alg_bytes(plate.n_hex, plate.n_coh, plate.n_nodes, plate.n_surf),
+            "parallelism": f"replicas x{ws}",
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "traffic": traffic, "kernel": "k_hex<float>",
+                     "alg_bytes_per_launch": alg, "launch_ms": hex_ms, "peak_kind": peak_kind},
+        "kernel_ms": {k: v[0] for k, v in prof.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                "seconds": t_e2e},
+        "gpu_launches": gpu_launches,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cores = len(os.sched_getaffinity(0))
+        rate, n, dt = oracle_rate(w, args.cpu_seconds, 10 ** 6, cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{n} explicit steps of the same workload from rest ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("pdn_kernels.cu", "pdn_internal.h"):
+        with open(os.path.join(ROOT, "paper_2301_05552_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gpu":
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_gpu(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

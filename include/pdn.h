@@ -1,0 +1,251 @@
+/*
+ * pdn.h - C ABI of the GB300 explicit impact step with partial
+ * Dirichlet-Neumann (PDN) contact.
+ *
+ * Method: Guillamet, Quintanas-Corominas, Rivero, Houzeaux, Vazquez, Turon,
+ * "Application of the partial Dirichlet-Neumann contact algorithm to simulate
+ * low-velocity impact events on composite structures", Composites Part A
+ * (2022), arXiv 2301.05552.  Section, equation and algorithm numbers below
+ * refer to that paper.
+ *
+ * One library context owns one laminated plate (hex8 plies, zero-thickness
+ * interface elements between plies of different angle), its lumped mass,
+ * its damage history and one rigid spherical striker, all resident in the
+ * memory of the current CUDA device.  Every per-step operation runs in the
+ * library's CUDA kernels on the stream given at creation.
+ *
+ * Conventions for every call:
+ *   - Units: mm, N, tonne, s, MPa.
+ *   - Return value 0 on success, a negative PDN_E_* code on failure; the
+ *     context's pdn_last_error() then holds a one-line message.  No C++
+ *     exception crosses this interface.
+ *   - Input arrays are owned by the caller and copied during the call;
+ *     output arrays are owned by the caller and written during the call.
+ *     Pointers are host pointers unless a parameter says otherwise.
+ *   - Node and element ids are the caller's (0-based) numbering.
+ *   - Nodal vector fields are structure-of-arrays: [3][n_nodes] doubles
+ *     (all x, then all y, then all z).
+ *   - Calls on one context are not thread-safe; distinct contexts are
+ *     independent.
+ */
+#ifndef PDN_H
+#define PDN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PDN_OK 0
+#define PDN_E_ARG (-1)           /* invalid argument, size or mesh */
+#define PDN_E_CUDA (-2)          /* CUDA runtime error (message says which) */
+#define PDN_E_OOM (-3)           /* device allocation failed */
+#define PDN_E_NONFINITE (-4)     /* a nodal acceleration or displacement became NaN/Inf */
+#define PDN_E_RELEASE_LIMIT (-5) /* a step still had adhesive contact nodes after
+                                    max_release_iters repetitions (Algorithm 2) */
+#define PDN_E_TIMEOUT (-6)       /* reserved: a bounded device wait gave up */
+#define PDN_E_UNSTABLE (-7)      /* material/mesh gives no stable step or a snap-back
+                                    softening law (2 E G <= lc X^2) */
+#define PDN_E_STATE (-8)         /* call out of order (e.g. step before set_impactor) */
+
+/* Precision of the element force, damage and cohesive updates.  Nodal
+ * displacement/velocity accumulation, the striker state and the contact gap
+ * test are always FP64. */
+#define PDN_FP64 0       /* element arithmetic in FP64 */
+#define PDN_FP32_FORCE 1 /* element arithmetic in FP32, nodal integration in FP64 */
+
+/* Fields for pdn_damage_field (one value per element, maximum over its
+ * integration points). */
+#define PDN_FIELD_D1 0   /* fibre damage max(d_FT, d_FC), per hex */
+#define PDN_FIELD_D2 1   /* matrix damage max(d_MT, d_MC), per hex */
+#define PDN_FIELD_D6 2   /* shear damage d_6, per hex */
+#define PDN_FIELD_DCOH 3 /* interface damage threshold r_D (Algorithm 5), per interface element */
+#define PDN_FIELD_PLASTIC 4 /* equivalent plastic shear strain, per hex */
+
+/* Kernel ids for pdn_profile_kernels. */
+#define PDN_K_CONTACT 0
+#define PDN_K_HEX 1
+#define PDN_K_COH 2
+#define PDN_K_GATHER 3
+#define PDN_K_TAIL 4
+#define PDN_K_COUNT 5
+
+typedef struct pdn_ctx pdn_ctx;
+
+/* Mesh of one plate (Sec. 2, Sec. 3.2).  All arrays are copied.
+ *   X         [3][n_nodes] reference coordinates (mm).
+ *   hex       [n_hex][8] hex8 connectivity: bottom face counter-clockwise
+ *             seen from +z, then the top face in the same order.
+ *   coh       [n_coh][8] zero-thickness interface elements: the 4 nodes of the
+ *             lower face, then the 4 coincident nodes of the upper face in the
+ *             same order.  May be NULL when n_coh == 0.
+ *   ply_of_hex [n_hex] ply index of each hex (0 <= ply < n_plies).
+ *   ply_angle_deg [n_plies] fibre angle of each ply about +z (degrees); the
+ *             material axes are fixed in the reference configuration.
+ *   fixed     [n_nodes] constraint bits: 1 = x, 2 = y, 4 = z held at zero
+ *             displacement (7 = clamped).  May be NULL (all free).
+ *   surf      [n_surf] ids of the contact-surface (slave) nodes. */
+typedef struct {
+  int64_t n_nodes, n_hex, n_coh, n_surf;
+  const double *X;
+  const int32_t *hex;
+  const int32_t *coh;
+  const int8_t *ply_of_hex;
+  const double *ply_angle_deg;
+  int32_t n_plies; /* 1..64 */
+  const uint8_t *fixed;
+  const int32_t *surf;
+} pdn_mesh_desc;
+
+/* Ply and interface material (Table 1 layout; MPa, N/mm, t/mm^3).
+ * Intralaminar law (Sec. 2.3.1, Algorithm 4): elastic constants, strengths,
+ * fracture angle alpha0, fracture toughnesses, shear yield stress Sp and
+ * hardening ratio Kp (hardening modulus Kp*G12).  Interface law (Sec. 2.3.2,
+ * Algorithm 5): GIc, GIIc, strengths tauI, tauII, Benzeggagh-Kenane
+ * exponent eta, penalty stiffness KI (mode I; the shear penalty follows as
+ * KI (GIc/GIIc)(tauII/tauI)^2).  Strengths XT, YT, SL of each hex are scaled
+ * by seeded factors uniform in [1 - spread, 1 + spread] (SplitMix64 of
+ * seed ^ (4*element + k), k = 0, 1, 2). */
+typedef struct {
+  double rho, E1, E2, E3, nu12, nu13, nu23, G12, G13, G23;
+  double XT, XC, YT, YC, SL, alpha0_deg;
+  double GXT, GXC, GYT, GYC, GSL;
+  double Sp, Kp;
+  double GIc, GIIc, tauI, tauII, eta, KI;
+  double spread;
+  uint64_t seed;
+} pdn_material;
+
+/* Run options.
+ *   precision       PDN_FP64 or PDN_FP32_FORCE.
+ *   damage_on       1: intralaminar and interface damage laws active.
+ *   plasticity_on   1: shear plasticity of Algorithm 4 active.
+ *   max_release_iters  repetitions of a step allowed for releasing adhesive
+ *                   contact nodes (Algorithm 2); 0 selects 8; a negative
+ *                   value allows none (the first adhesive node is an error).
+ *   phi             Tchamwa-Wielgosz parameter (Sec. 2.2.1); 1 = central
+ *                   difference; 0 selects 1.
+ *   dt              time step (s); 0 = dt_safety * min(dt_bulk, dt_coh).
+ *   dt_safety       factor on the stable step; 0 selects 0.5.
+ *   gravity         body acceleration (mm/s^2) on plate and striker.
+ *   history_cap     number of per-step contact-force samples kept on the
+ *                   device; 0 selects 1<<20.
+ *   stream          cudaStream_t on which all work is issued (NULL = the
+ *                   legacy default stream). */
+typedef struct {
+  int32_t precision;
+  int32_t damage_on;
+  int32_t plasticity_on;
+  int32_t max_release_iters;
+  double phi;
+  double dt;
+  double dt_safety;
+  double gravity[3];
+  int64_t history_cap;
+  void *stream;
+} pdn_options;
+
+/* Counters and derived quantities of a context. */
+typedef struct {
+  double dt, dt_bulk, dt_coh;
+  double time;
+  double f_peak;           /* maximum contact force along the impact axis so far */
+  int64_t step;            /* committed steps */
+  int64_t n_active;        /* contact nodes at the last committed step */
+  int64_t n_repeats;       /* step repetitions for node release so far */
+  int64_t n_nodes, n_hex, n_coh, n_surf;
+  int64_t device_bytes;    /* device memory held by the context */
+  int32_t status;          /* sticky device status (PDN_OK or an error code) */
+  int32_t precision;
+} pdn_info;
+
+/* Create a context on the current CUDA device: validate and copy the mesh,
+ * compute the lumped (row-sum) mass, the characteristic lengths and stable
+ * steps (Sec. 2.3.1: dt = lc sqrt(rho/max Cij), lc = V^(1/3); Sec. 2.3.2:
+ * dt_coh = sqrt(rho_bar/K) with rho_bar = rho * adjacent hex thickness), the
+ * node-to-element CSR map used for the deterministic force gather, and
+ * allocate all device state (displacement, velocity, history double buffers).
+ * Initial state: d = v = 0, damage thresholds r = 1, plastic strain 0,
+ * interface thresholds 0 (Algorithms 4, 5).  On failure *out is NULL. */
+int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat,
+                  const pdn_options *opt);
+
+/* Set the rigid spherical striker (Sec. 2.2.2): radius (mm), mass (t),
+ * centre (mm) and velocity (mm/s).  The striker moves only along the unit
+ * vector of its initial velocity (its other degrees of freedom are held, as
+ * in Sec. 3.2); a zero velocity selects -z.  Resets the contact force to 0. */
+int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double centre[3],
+                     const double velocity[3]);
+
+/* Advance nsteps explicit steps (Algorithm 1 per step): striker RK4 update
+ * with the previous contact force (Eq. rk4); contact detection and
+ * projection of penetrated and still-active surface nodes onto the sphere
+ * (Dirichlet condition, Sec. 2.1); hex8 and interface internal forces with
+ * trial damage history; deterministic CSR gather; lumped-mass accelerations
+ * with the contact reactions; release of adhesive nodes (f^c . n < 0,
+ * Eq. anodes) with repetition of the step (Algorithm 2); Tchamwa-Wielgosz
+ * update (Sec. 2.2.1).  Returns after the work has completed on the stream.
+ * Errors: PDN_E_STATE without a striker, PDN_E_NONFINITE,
+ * PDN_E_RELEASE_LIMIT (both sticky), PDN_E_CUDA. */
+int pdn_step(pdn_ctx *ctx, int64_t nsteps);
+
+/* Contact force of the striker on the plate (Sec. 2.2.2: f^e = sum_j f^c_j):
+ * f_now[3] at the last committed step, *f_peak the largest component along
+ * the impact axis so far, and history[k] (k < cap) the component along the
+ * impact axis after step k+1.  Any output pointer may be NULL.  Returns the
+ * number of history samples written (>= 0), or, when history is NULL, the
+ * number of samples available; negative values are error codes. */
+int64_t pdn_contact_force(pdn_ctx *ctx, double f_now[3], double *f_peak, double *history,
+                          int64_t cap);
+
+/* Damage field `which` (PDN_FIELD_*), one float per hex (or per interface
+ * element for PDN_FIELD_DCOH): the maximum over the element's integration
+ * points of the committed history.  n must equal the element count of the
+ * field.  out is a device pointer when out_on_device != 0. */
+int pdn_damage_field(pdn_ctx *ctx, int32_t which, float *out, int64_t n, int32_t out_on_device);
+
+/* Committed state: displacement d and velocity v ([3][n_nodes], the
+ * Tchamwa-Wielgosz velocity of Sec. 2.2.1) and imp[10] = striker centre[3],
+ * velocity[3], contact force[3], time.  Any pointer may be NULL. */
+int pdn_get_state(pdn_ctx *ctx, double *d, double *v, double *imp);
+
+/* Install displacement and velocity ([3][n_nodes]; constrained degrees of
+ * freedom are forced to zero) and recompute the acceleration from the
+ * internal forces without contact, as at a restart.  History and contact
+ * set are kept. */
+int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v);
+
+/* Contact set of the last committed step: active[n_surf] (1 = in contact)
+ * and the reaction magnitude lambda[n_surf] along each node's sphere normal
+ * (0 where inactive).  Either pointer may be NULL. */
+int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda);
+
+/* Nodal internal force f^i ([3][n_nodes]) at the committed state, computed
+ * by the same element and gather kernels as a step, without advancing and
+ * without changing the history. */
+int pdn_internal_force(pdn_ctx *ctx, double *f_int);
+
+/* Counters; see pdn_info. */
+int pdn_get_info(pdn_ctx *ctx, pdn_info *info);
+
+/* Advance nsteps steps launching each kernel directly (no graph) with CUDA
+ * events around every launch on the context's stream, and return the mean
+ * device time per launch of each kernel in ms_per_launch[PDN_K_COUNT] and
+ * the launch counts in launches[PDN_K_COUNT] (either may be NULL).  The
+ * steps are real steps of the simulation. */
+int pdn_profile_kernels(pdn_ctx *ctx, int64_t nsteps, float *ms_per_launch, int64_t *launches);
+
+/* Release all device memory of the context.  NULL is ignored. */
+void pdn_destroy(pdn_ctx *ctx);
+
+/* Last error message of a context (never NULL); with ctx == NULL, the last
+ * error of a failed pdn_init_mesh in this thread. */
+const char *pdn_last_error(const pdn_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDN_H */

@@ -196,9 +196,24 @@ static double softening_A(double lc, double X, double E, double G) {
   return 2.0 * lc * X * X / (2.0 * E * G - lc * X * X);
 }
 
+static void cdm_point_c(const orc_material *m, const double C0[6][6], const double H[6][6],
+                        double lc, const double sf[3], const double eps[6], const double hin[NH],
+                        double hout[NH], double sig[6], int damage_on, int plasticity_on);
+
 void orc_cdm_point(const orc_material *m, double lc, const double sf[3], const double eps[6],
                    const double hin[NH], double hout[NH], double sig[6], int damage_on,
                    int plasticity_on) {
+  double C0[6][6], H[6][6];
+  orc_stiffness(m, C0);
+  orc_compliance(m, H);
+  cdm_point_c(m, C0, H, lc, sf, eps, hin, hout, sig, damage_on, plasticity_on);
+}
+
+/* Same, with the undamaged stiffness C0 and compliance H of the material
+ * passed in (computed once per element). */
+static void cdm_point_c(const orc_material *m, const double C0[6][6], const double H[6][6],
+                        double lc, const double sf[3], const double eps[6], const double hin[NH],
+                        double hout[NH], double sig[6], int damage_on, int plasticity_on) {
   double XT = m->XT * sf[0], YT = m->YT * sf[1], SL = m->SL * sf[2];
   double rFT = hin[0], rFC = hin[1], rMT = hin[2], rMC = hin[3];
   double gp12 = hin[4], gp13 = hin[5], pbar = hin[6];
@@ -218,8 +233,6 @@ void orc_cdm_point(const orc_material *m, double lc, const double sf[3], const d
   }
   /* 2. elastic strain and effective stress */
   double ee[6] = {eps[0], eps[1], eps[2], eps[3] - gp12, eps[4] - gp13, eps[5]};
-  double C0[6][6];
-  orc_stiffness(m, C0);
   double se[6];
   for (int i = 0; i < 6; ++i) {
     se[i] = 0.0;
@@ -269,8 +282,6 @@ void orc_cdm_point(const orc_material *m, double lc, const double sf[3], const d
   }
   /* 6. nominal stress through the damaged compliance */
   double q[3] = {1.0 - D1, 1.0 - D2, 1.0};
-  double H[6][6];
-  orc_compliance(m, H);
   double M3[3][3], rhs[3], sn[3];
   for (int i = 0; i < 3; ++i) {
     for (int j = 0; j < 3; ++j) M3[i][j] = (i == j) ? H[i][i] : q[i] * H[i][j];
@@ -401,6 +412,9 @@ double orc_hex8_force(const orc_material *m, double angle_deg, double lc, const 
   double c = cos(th), s = sin(th);
   /* columns of R are the ply axes in global coordinates */
   double R[3][3] = {{c, -s, 0.0}, {s, c, 0.0}, {0.0, 0.0, 1.0}};
+  double C0[6][6], Hc[6][6];
+  orc_stiffness(m, C0);
+  orc_compliance(m, Hc);
   double energy = 0.0;
   for (int a = 0; a < 8; ++a) f[a][0] = f[a][1] = f[a][2] = 0.0;
   for (int g = 0; g < 8; ++g) {
@@ -431,7 +445,7 @@ double orc_hex8_force(const orc_material *m, double angle_deg, double lc, const 
       }
     double eps[6] = {Em[0][0], Em[1][1], Em[2][2], 2.0 * Em[0][1], 2.0 * Em[0][2], 2.0 * Em[1][2]};
     double sig[6];
-    orc_cdm_point(m, lc, sf, eps, hin + g * NH, hout + g * NH, sig, damage_on, plasticity_on);
+    cdm_point_c(m, C0, Hc, lc, sf, eps, hin + g * NH, hout + g * NH, sig, damage_on, plasticity_on);
     double Sm[3][3] = {{sig[0], sig[3], sig[4]}, {sig[3], sig[1], sig[5]}, {sig[4], sig[5], sig[2]}};
     /* back to global axes: S = R Sm R^T */
     double S[3][3];

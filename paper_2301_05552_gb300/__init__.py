@@ -1,0 +1,322 @@
+"""GB300-native explicit impact step with partial Dirichlet-Neumann contact.
+
+Python binding of the C ABI declared in ``include/pdn.h`` (ctypes).  The
+functions here carry the same names as the C entry points and only marshal
+arguments: every step of the method runs in the CUDA kernels of
+``lib/libpdn.so``.  There is no CPU fallback; a missing or unloadable library
+raises.
+
+Method: Guillamet et al., "Application of the partial Dirichlet-Neumann
+contact algorithm to simulate low-velocity impact events on composite
+structures", Composites Part A (2022), arXiv 2301.05552.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "PdnError", "lib", "build",
+    "pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
+    "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
+    "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
+    "PDN_FP64", "PDN_FP32_FORCE", "FIELDS", "KERNELS",
+]
+
+PDN_FP64 = 0
+PDN_FP32_FORCE = 1
+FIELDS = {"D1": 0, "D2": 1, "D6": 2, "DCOH": 3, "PLASTIC": 4}
+KERNELS = ["contact", "hex", "coh", "gather", "tail"]
+ERRORS = {-1: "PDN_E_ARG", -2: "PDN_E_CUDA", -3: "PDN_E_OOM", -4: "PDN_E_NONFINITE",
+          -5: "PDN_E_RELEASE_LIMIT", -6: "PDN_E_TIMEOUT", -7: "PDN_E_UNSTABLE", -8: "PDN_E_STATE"}
+EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
+           "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
+           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error"]
+
+
+class PdnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
+                ("X", C.POINTER(C.c_double)), ("hex", C.POINTER(C.c_int32)), ("coh", C.POINTER(C.c_int32)),
+                ("ply_of_hex", C.POINTER(C.c_int8)), ("ply_angle_deg", C.POINTER(C.c_double)),
+                ("n_plies", C.c_int32), ("fixed", C.POINTER(C.c_uint8)), ("surf", C.POINTER(C.c_int32))]
+
+
+MATERIAL_KEYS = ("rho", "E1", "E2", "E3", "nu12", "nu13", "nu23", "G12", "G13", "G23",
+                 "XT", "XC", "YT", "YC", "SL", "alpha0_deg", "GXT", "GXC", "GYT", "GYC", "GSL",
+                 "Sp", "Kp", "GIc", "GIIc", "tauI", "tauII", "eta", "KI", "spread")
+
+
+class Material(C.Structure):
+    _fields_ = [(k, C.c_double) for k in MATERIAL_KEYS] + [("seed", C.c_uint64)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("damage_on", C.c_int32), ("plasticity_on", C.c_int32),
+                ("max_release_iters", C.c_int32), ("phi", C.c_double), ("dt", C.c_double),
+                ("dt_safety", C.c_double), ("gravity", C.c_double * 3), ("history_cap", C.c_int64),
+                ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("dt", C.c_double), ("dt_bulk", C.c_double), ("dt_coh", C.c_double), ("time", C.c_double),
+                ("f_peak", C.c_double), ("step", C.c_int64), ("n_active", C.c_int64), ("n_repeats", C.c_int64),
+                ("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
+                ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def lib():
+    """Load lib/libpdn.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if _build._stale():
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library {path} is missing; run paper_2301_05552_gb300.build()")
+            L = C.CDLL(path)
+            vp, dp = C.c_void_p, C.POINTER(C.c_double)
+            L.pdn_init_mesh.argtypes = [C.POINTER(vp), C.POINTER(MeshDesc), C.POINTER(Material), C.POINTER(Options)]
+            L.pdn_set_impactor.argtypes = [vp, C.c_double, C.c_double, dp, dp]
+            L.pdn_step.argtypes = [vp, C.c_int64]
+            L.pdn_contact_force.argtypes = [vp, dp, dp, dp, C.c_int64]
+            L.pdn_contact_force.restype = C.c_int64
+            L.pdn_damage_field.argtypes = [vp, C.c_int32, C.c_void_p, C.c_int64, C.c_int32]
+            L.pdn_get_state.argtypes = [vp, dp, dp, dp]
+            L.pdn_set_state.argtypes = [vp, dp, dp]
+            L.pdn_get_contact.argtypes = [vp, C.POINTER(C.c_uint8), dp]
+            L.pdn_internal_force.argtypes = [vp, dp]
+            L.pdn_get_info.argtypes = [vp, C.POINTER(Info)]
+            L.pdn_profile_kernels.argtypes = [vp, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_int64)]
+            L.pdn_destroy.argtypes = [vp]
+            L.pdn_destroy.restype = None
+            L.pdn_last_error.argtypes = [vp]
+            L.pdn_last_error.restype = C.c_char_p
+            for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
+                         "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
+                         "pdn_init_mesh"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+def _check(ctx, rc):
+    if rc < 0:
+        msg = lib().pdn_last_error(ctx.handle if ctx is not None else None)
+        raise PdnError(int(rc), (msg or b"").decode())
+    return rc
+
+
+class Context:
+    """A pdn_ctx handle (one plate + one striker on the current device)."""
+
+    def __init__(self, handle, n_nodes, n_hex, n_coh, n_surf, stream):
+        self.handle = handle
+        self.n_nodes, self.n_hex, self.n_coh, self.n_surf = n_nodes, n_hex, n_coh, n_surf
+        self.stream = stream
+
+    def close(self):
+        if self.handle:
+            lib().pdn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream or None
+    except Exception:
+        pass
+    return None
+
+
+def pdn_init_mesh(plate, material: dict, precision: int = PDN_FP32_FORCE, damage_on: bool = True,
+                  plasticity_on: bool = True, max_release_iters: int = 8, phi: float = 1.0, dt: float = 0.0,
+                  dt_safety: float = 0.5, gravity=(0.0, 0.0, 0.0), history_cap: int = 1 << 20,
+                  stream: Optional[int] = None) -> Context:
+    """pdn_init_mesh: ``plate`` is any object with the fields of
+    pdn_inputs.Plate (X [3,n], hex [n,8], coh [m,8], ply_of_hex, ply_angle_deg,
+    fixed, surf)."""
+    L = lib()
+    keep = dict(
+        X=np.ascontiguousarray(plate.X, dtype=np.float64),
+        hex=np.ascontiguousarray(plate.hex, dtype=np.int32).reshape(-1, 8),
+        coh=np.ascontiguousarray(plate.coh, dtype=np.int32).reshape(-1, 8),
+        ply=np.ascontiguousarray(plate.ply_of_hex, dtype=np.int8),
+        ang=np.ascontiguousarray(plate.ply_angle_deg, dtype=np.float64),
+        fixed=np.ascontiguousarray(plate.fixed, dtype=np.uint8),
+        surf=np.ascontiguousarray(plate.surf, dtype=np.int32),
+    )
+    m = MeshDesc()
+    m.n_nodes = keep["X"].shape[1]
+    m.n_hex = keep["hex"].shape[0]
+    m.n_coh = keep["coh"].shape[0]
+    m.n_surf = keep["surf"].shape[0]
+    m.X = _ptr(keep["X"], C.c_double)
+    m.hex = _ptr(keep["hex"], C.c_int32)
+    m.coh = _ptr(keep["coh"], C.c_int32) if m.n_coh else None
+    m.ply_of_hex = _ptr(keep["ply"], C.c_int8)
+    m.ply_angle_deg = _ptr(keep["ang"], C.c_double)
+    m.n_plies = keep["ang"].shape[0]
+    m.fixed = _ptr(keep["fixed"], C.c_uint8)
+    m.surf = _ptr(keep["surf"], C.c_int32) if m.n_surf else None
+    mat = Material()
+    for k in MATERIAL_KEYS:
+        setattr(mat, k, float(material[k]))
+    mat.seed = int(material["seed"])
+    o = Options()
+    o.precision, o.damage_on, o.plasticity_on = int(precision), int(damage_on), int(plasticity_on)
+    o.max_release_iters, o.phi, o.dt, o.dt_safety = int(max_release_iters), float(phi), float(dt), float(dt_safety)
+    for i in range(3):
+        o.gravity[i] = float(gravity[i])
+    o.history_cap = int(history_cap)
+    if stream is None:
+        stream = _current_stream()
+    o.stream = stream
+    h = C.c_void_p()
+    rc = L.pdn_init_mesh(C.byref(h), C.byref(m), C.byref(mat), C.byref(o))
+    if rc < 0:
+        raise PdnError(rc, (L.pdn_last_error(None) or b"").decode())
+    return Context(h, m.n_nodes, m.n_hex, m.n_coh, m.n_surf, stream)
+
+
+def pdn_set_impactor(ctx: Context, radius: float, mass: float, centre, velocity):
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    w = np.ascontiguousarray(velocity, dtype=np.float64)
+    _check(ctx, lib().pdn_set_impactor(ctx.handle, float(radius), float(mass), _ptr(c, C.c_double),
+                                       _ptr(w, C.c_double)))
+
+
+def pdn_step(ctx: Context, nsteps: int):
+    _check(ctx, lib().pdn_step(ctx.handle, int(nsteps)))
+
+
+def pdn_contact_force(ctx: Context, cap: Optional[int] = None):
+    """(f_now[3], f_peak, history[:n]) of the striker-plate contact force."""
+    L = lib()
+    f = np.zeros(3)
+    pk = np.zeros(1)
+    n_avail = _check(ctx, L.pdn_contact_force(ctx.handle, _ptr(f, C.c_double), _ptr(pk, C.c_double), None, 0))
+    cap = n_avail if cap is None else min(cap, n_avail)
+    hist = np.zeros(max(cap, 1))
+    n = _check(ctx, L.pdn_contact_force(ctx.handle, None, None, _ptr(hist, C.c_double), cap)) if cap > 0 else 0
+    return f, float(pk[0]), hist[:n]
+
+
+def pdn_damage_field(ctx: Context, which, out=None):
+    """Damage field as a float32 numpy array (host) or into a CUDA torch
+    tensor ``out`` (device pointer path)."""
+    w = FIELDS[which] if isinstance(which, str) else int(which)
+    n = ctx.n_coh if w == FIELDS["DCOH"] else ctx.n_hex
+    if out is not None and hasattr(out, "data_ptr"):
+        _check(ctx, lib().pdn_damage_field(ctx.handle, w, C.c_void_p(out.data_ptr()), n, 1))
+        return out
+    a = np.zeros(n, dtype=np.float32)
+    _check(ctx, lib().pdn_damage_field(ctx.handle, w, a.ctypes.data_as(C.c_void_p), n, 0))
+    return a
+
+
+def pdn_get_state(ctx: Context):
+    d = np.zeros((3, ctx.n_nodes))
+    v = np.zeros((3, ctx.n_nodes))
+    imp = np.zeros(10)
+    _check(ctx, lib().pdn_get_state(ctx.handle, _ptr(d, C.c_double), _ptr(v, C.c_double), _ptr(imp, C.c_double)))
+    return d, v, dict(centre=imp[0:3].copy(), velocity=imp[3:6].copy(), force=imp[6:9].copy(), time=imp[9])
+
+
+def pdn_set_state(ctx: Context, d, v):
+    d = np.ascontiguousarray(d, dtype=np.float64).reshape(3, ctx.n_nodes)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(3, ctx.n_nodes)
+    _check(ctx, lib().pdn_set_state(ctx.handle, _ptr(d, C.c_double), _ptr(v, C.c_double)))
+
+
+def pdn_get_contact(ctx: Context):
+    act = np.zeros(max(ctx.n_surf, 1), dtype=np.uint8)
+    lam = np.zeros(max(ctx.n_surf, 1))
+    _check(ctx, lib().pdn_get_contact(ctx.handle, _ptr(act, C.c_uint8), _ptr(lam, C.c_double)))
+    return act[: ctx.n_surf], lam[: ctx.n_surf]
+
+
+def pdn_internal_force(ctx: Context):
+    f = np.zeros((3, ctx.n_nodes))
+    _check(ctx, lib().pdn_internal_force(ctx.handle, _ptr(f, C.c_double)))
+    return f
+
+
+def pdn_get_info(ctx: Context) -> dict:
+    info = Info()
+    _check(ctx, lib().pdn_get_info(ctx.handle, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in Info._fields_}
+
+
+def pdn_profile_kernels(ctx: Context, nsteps: int):
+    ms = (C.c_float * 5)()
+    cnt = (C.c_int64 * 5)()
+    _check(ctx, lib().pdn_profile_kernels(ctx.handle, int(nsteps), ms, cnt))
+    return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNELS)}
+
+
+def pdn_destroy(ctx: Context):
+    ctx.close()
+
+
+def pdn_last_error(ctx: Optional[Context]) -> str:
+    return (lib().pdn_last_error(ctx.handle if ctx is not None else None) or b"").decode()
+
+
+class Solver:
+    """Convenience wrapper: one context for a pdn_inputs.Workload."""
+
+    def __init__(self, workload, precision=None, **kw):
+        prec = precision if precision is not None else (PDN_FP64 if workload.fp64 else PDN_FP32_FORCE)
+        self.workload = workload
+        self.ctx = pdn_init_mesh(workload.plate, workload.material, precision=prec,
+                                 damage_on=workload.damage_on, plasticity_on=workload.plasticity_on,
+                                 phi=workload.phi, dt_safety=workload.dt_safety, gravity=workload.gravity, **kw)
+        pdn_set_impactor(self.ctx, *workload.impactor())
+
+    def step(self, n):
+        pdn_step(self.ctx, n)
+
+    def info(self):
+        return pdn_get_info(self.ctx)
+
+    def state(self):
+        return pdn_get_state(self.ctx)
+
+    def force_history(self):
+        return pdn_contact_force(self.ctx)[2]
+
+    def close(self):
+        self.ctx.close()

@@ -1,0 +1,921 @@
+// Host runtime and C ABI (include/pdn.h) of the GB300 explicit PDN impact step.
+//
+// Set-up (lumped mass, stable steps, node-to-element CSR, constants) runs once
+// on the host in pdn_init_mesh; every per-step operation runs in the kernels of
+// pdn_kernels.cu.  pdn_step replays a captured CUDA graph of passes; the
+// device-side state machine decides advance / repeat / halt, so the host only
+// checks the committed step count once per call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pdn.h"
+#include "pdn_internal.h"
+
+using namespace pdn;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+constexpr int kGatherBlock = 256;
+constexpr int kGraphPasses = 32;
+constexpr int kProfilePasses = 64;
+
+// Arena of device memory: one cudaMalloc, 256-byte aligned sub-allocations.
+struct Arena {
+  char *base = nullptr;
+  size_t size = 0, used = 0;
+  template <typename P>
+  P *take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return base ? reinterpret_cast<P *>(base + off) : nullptr;
+  }
+};
+
+__global__ void k_fill_hist_float(float *h, int64_t per_field, int64_t n_init_fields) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < per_field * 7) h[i] = (i < per_field * n_init_fields) ? 1.0f : 0.0f;
+}
+__global__ void k_fill_hist_double(double *h, int64_t per_field, int64_t n_init_fields) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < per_field * 7) h[i] = (i < per_field * n_init_fields) ? 1.0 : 0.0;
+}
+template <typename V4>
+__global__ void k_mirror(const double *d, V4 *u, int64_t nn) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nn) return;
+  V4 o;
+  o.x = d[j];
+  o.y = d[nn + j];
+  o.z = d[2 * nn + j];
+  o.w = 0;
+  u[j] = o;
+}
+__global__ void k_set_mode(Ctl *ctl, int32_t mode, int64_t target) {
+  if (ctl->mode == MODE_HALT) return;
+  ctl->mode = mode;
+  ctl->target = target;
+}
+
+inline int grid_of(int64_t n, int b) {
+  int64_t g = (n + b - 1) / b;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+struct pdn_ctx {
+  int precision = PDN_FP32_FORCE;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t nn = 0, nh = 0, nc = 0, ns = 0;
+  Arena arena;
+  Dev<float> Df{};
+  Dev<double> Dd{};
+  Mat<float> Mf{};
+  Mat<double> Md{};
+  Ctl *ctl_dev = nullptr;
+  Ctl *ctl_host = nullptr;  // pinned
+  Striker *imp_dev = nullptr;
+  float *field = nullptr;
+  double dt = 0, dt_bulk = 0, dt_coh = 0, phi = 1;
+  double grav[3] = {0, 0, 0};
+  int max_repeats = 8;
+  int64_t hist_cap = 0;
+  bool has_imp = false;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<cudaEvent_t> prof_ev;
+  std::string err;
+
+  // Pointers common to both precisions.
+  template <typename F>
+  void both(F &&f) {
+    f(Df);
+    f(Dd);
+  }
+};
+
+namespace {
+
+int fail(pdn_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(pdn_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, PDN_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PDN_CU(call, where)                      \
+  do {                                           \
+    cudaError_t _e = (call);                     \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+cudaError_t run_pass(pdn_ctx *ctx, cudaEvent_t *ev) {
+  if (ctx->precision == PDN_FP64) return launch_pass<double>(ctx->Dd, ctx->Md, ctx->stream, kGatherBlock, ev);
+  return launch_pass<float>(ctx->Df, ctx->Mf, ctx->stream, kGatherBlock, ev);
+}
+
+cudaError_t build_graph(pdn_ctx *ctx) {
+  if (ctx->graph) return cudaSuccess;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < kGraphPasses; ++k) {
+    e = run_pass(ctx, nullptr);
+    if (e != cudaSuccess) break;
+  }
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  return e;
+}
+
+// Launch n passes: whole graphs, then single passes for the remainder.
+cudaError_t launch_passes(pdn_ctx *ctx, int64_t n) {
+  cudaError_t e = build_graph(ctx);
+  if (e != cudaSuccess) return e;
+  for (int64_t k = 0; k + kGraphPasses <= n; k += kGraphPasses) {
+    e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
+  for (int64_t k = 0; k < n % kGraphPasses; ++k) {
+    e = run_pass(ctx, nullptr);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int read_ctl(pdn_ctx *ctx) {
+  PDN_CU(cudaMemcpyAsync(ctx->ctl_host, ctx->ctl_dev, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream),
+         "read control block");
+  PDN_CU(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+  return PDN_OK;
+}
+
+int set_mode(pdn_ctx *ctx, int32_t mode, int64_t target) {
+  k_set_mode<<<1, 1, 0, ctx->stream>>>(ctx->ctl_dev, mode, target);
+  PDN_CU(cudaGetLastError(), "set mode");
+  return PDN_OK;
+}
+
+// Material constants in precision T from the double-precision record.
+template <typename T>
+int fill_mat(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_plies, int damage_on,
+             int plasticity_on, std::string &why) {
+  double H[3][3] = {{1 / m.E1, -m.nu12 / m.E1, -m.nu13 / m.E1},
+                    {-m.nu12 / m.E1, 1 / m.E2, -m.nu23 / m.E2},
+                    {-m.nu13 / m.E1, -m.nu23 / m.E2, 1 / m.E3}};
+  double det = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) - H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+               H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+  if (!(det > 0)) {
+    why = "elastic constants give a non positive-definite compliance";
+    return PDN_E_ARG;
+  }
+  double C[3][3];
+  C[0][0] = (H[1][1] * H[2][2] - H[1][2] * H[2][1]) / det;
+  C[0][1] = (H[0][2] * H[2][1] - H[0][1] * H[2][2]) / det;
+  C[0][2] = (H[0][1] * H[1][2] - H[0][2] * H[1][1]) / det;
+  C[1][1] = (H[0][0] * H[2][2] - H[0][2] * H[2][0]) / det;
+  C[1][2] = (H[0][2] * H[1][0] - H[0][0] * H[1][2]) / det;
+  C[2][2] = (H[0][0] * H[1][1] - H[0][1] * H[1][0]) / det;
+  M.C11 = (T)C[0][0];
+  M.C12 = (T)C[0][1];
+  M.C13 = (T)C[0][2];
+  M.C22 = (T)C[1][1];
+  M.C23 = (T)C[1][2];
+  M.C33 = (T)C[2][2];
+  M.G12 = (T)m.G12;
+  M.G13 = (T)m.G13;
+  M.G23 = (T)m.G23;
+  M.h11 = (T)H[0][0];
+  M.h22 = (T)H[1][1];
+  M.h33 = (T)H[2][2];
+  M.h12 = (T)H[0][1];
+  M.h13 = (T)H[0][2];
+  M.h23 = (T)H[1][2];
+  M.E1 = (T)m.E1;
+  M.E2 = (T)m.E2;
+  M.XT = (T)m.XT;
+  M.XC = (T)m.XC;
+  M.YT = (T)m.YT;
+  M.YC = (T)m.YC;
+  M.SL = (T)m.SL;
+  M.GXT = (T)m.GXT;
+  M.GXC = (T)m.GXC;
+  M.GYT = (T)m.GYT;
+  M.GYC = (T)m.GYC;
+  M.GSL = (T)m.GSL;
+  const double a0 = m.alpha0_deg * M_PI / 180.0;
+  const double ca = std::cos(a0), sa = std::sin(a0), t2 = std::tan(2.0 * a0);
+  M.ca = (T)ca;
+  M.sa = (T)sa;
+  M.etaT = (T)(-1.0 / t2);
+  M.ST = (T)(m.YC * ca * (sa + ca / t2));
+  M.etaLc = (T)(-std::cos(2.0 * a0) / (m.YC * ca * ca));
+  M.g = (T)(m.GYT / m.GSL);
+  M.Sp = (T)m.Sp;
+  M.Kp = (T)m.Kp;
+  const double KI = m.KI;
+  const double Ksh = KI * (m.GIc / m.GIIc) * (m.tauII / m.tauI) * (m.tauII / m.tauI);
+  const double D3o = m.tauI / KI, D3c = 2.0 * m.GIc / m.tauI;
+  const double Dsho = m.tauII / Ksh, Dshc = 2.0 * m.GIIc / m.tauII;
+  M.KI = (T)KI;
+  M.Ksh = (T)Ksh;
+  M.KI_D3o2 = (T)(KI * D3o * D3o);
+  M.Ksh_Dsho2 = (T)(Ksh * Dsho * Dsho);
+  M.KI_D3oD3c = (T)(KI * D3o * D3c);
+  M.Ksh_DshoDshc = (T)(Ksh * Dsho * Dshc);
+  M.eta = (T)m.eta;
+  M.onset_floor = (T)(0.999 * std::min(KI * D3o * D3o, Ksh * Dsho * Dsho));
+  M.spread = (T)m.spread;
+  M.seed = m.seed;
+  M.damage_on = damage_on;
+  M.plasticity_on = plasticity_on;
+  for (int p = 0; p < kMaxPlies; ++p) {
+    const double th = p < n_plies ? ply_angle[p] * M_PI / 180.0 : 0.0;
+    M.ply_c[p] = (T)std::cos(th);
+    M.ply_s[p] = (T)std::sin(th);
+  }
+  return PDN_OK;
+}
+
+// Hex8 geometry on the host (set-up only): det J and N_a at the 2x2x2 points.
+void hex_gauss(const double X[8][3], double detJ[8], double N[8][8]) {
+  static const int S[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                              {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+  const double gp = 1.0 / std::sqrt(3.0);
+  for (int g = 0; g < 8; ++g) {
+    const double xi = S[g][0] * gp, et = S[g][1] * gp, ze = S[g][2] * gp;
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < 8; ++a) {
+      const double sx = S[a][0], sy = S[a][1], sz = S[a][2];
+      const double dN[3] = {0.125 * sx * (1 + et * sy) * (1 + ze * sz), 0.125 * sy * (1 + xi * sx) * (1 + ze * sz),
+                            0.125 * sz * (1 + xi * sx) * (1 + et * sy)};
+      N[g][a] = 0.125 * (1 + xi * sx) * (1 + et * sy) * (1 + ze * sz);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) J[i][k] += X[a][i] * dN[k];
+    }
+    detJ[g] = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pdn_last_error(const pdn_ctx *ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return ctx->err.c_str();
+}
+
+void pdn_destroy(pdn_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->arena.base) cudaFree(ctx->arena.base);
+  if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat, const pdn_options *opt) {
+  g_init_error.clear();
+  if (!out) {
+    g_init_error = "out is NULL";
+    return PDN_E_ARG;
+  }
+  *out = nullptr;
+  auto bad = [](const std::string &m) {
+    g_init_error = m;
+    return PDN_E_ARG;
+  };
+  if (!mesh || !mat || !opt) return bad("mesh, material and options are required");
+  const int64_t nn = mesh->n_nodes, nh = mesh->n_hex, nc = mesh->n_coh, ns = mesh->n_surf;
+  if (nn <= 0 || nh <= 0 || nc < 0 || ns < 0) return bad("need n_nodes > 0, n_hex > 0, n_coh >= 0, n_surf >= 0");
+  if (nn >= (int64_t)INT32_MAX || (nh + nc) * 8 >= (int64_t)INT32_MAX)
+    return bad("mesh too large for 32-bit node/slot ids");
+  if (!mesh->X || !mesh->hex || !mesh->ply_of_hex || !mesh->ply_angle_deg) return bad("X, hex, ply_of_hex, ply_angle_deg are required");
+  if (nc > 0 && !mesh->coh) return bad("coh is NULL with n_coh > 0");
+  if (ns > 0 && !mesh->surf) return bad("surf is NULL with n_surf > 0");
+  if (mesh->n_plies < 1 || mesh->n_plies > kMaxPlies) return bad("n_plies must be in 1..64");
+  if (opt->precision != PDN_FP64 && opt->precision != PDN_FP32_FORCE) return bad("unknown precision");
+  for (int64_t k = 0; k < nh * 8; ++k)
+    if (mesh->hex[k] < 0 || mesh->hex[k] >= nn) return bad("hex node id out of range");
+  for (int64_t k = 0; k < nc * 8; ++k)
+    if (mesh->coh[k] < 0 || mesh->coh[k] >= nn) return bad("interface node id out of range");
+  for (int64_t e = 0; e < nh; ++e)
+    if (mesh->ply_of_hex[e] < 0 || mesh->ply_of_hex[e] >= mesh->n_plies) return bad("ply id out of range");
+  std::vector<int32_t> surf_of(nn, -1);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t j = mesh->surf[s];
+    if (j < 0 || j >= nn) return bad("surface node id out of range");
+    if (surf_of[j] >= 0) return bad("duplicate surface node id");
+    surf_of[j] = (int32_t)s;
+  }
+  if (mesh->fixed)
+    for (int64_t j = 0; j < nn; ++j)
+      if (mesh->fixed[j] > 7) return bad("fixed entries must be constraint bits 0..7");
+  const pdn_material &m = *mat;
+  if (!(m.rho > 0 && m.E1 > 0 && m.E2 > 0 && m.E3 > 0 && m.G12 > 0 && m.G13 > 0 && m.G23 > 0))
+    return bad("density and moduli must be positive");
+  if (!(m.KI > 0 && m.tauI > 0 && m.tauII > 0 && m.GIc > 0 && m.GIIc > 0)) return bad("interface constants must be positive");
+
+  pdn_ctx *ctx = new (std::nothrow) pdn_ctx();
+  if (!ctx) return bad("host allocation failed");
+  ctx->precision = opt->precision;
+  ctx->nn = nn;
+  ctx->nh = nh;
+  ctx->nc = nc;
+  ctx->ns = ns;
+  ctx->phi = opt->phi == 0.0 ? 1.0 : opt->phi;
+  for (int i = 0; i < 3; ++i) ctx->grav[i] = opt->gravity[i];
+  ctx->max_repeats = opt->max_release_iters > 0 ? opt->max_release_iters : (opt->max_release_iters < 0 ? 0 : 8);
+  ctx->hist_cap = opt->history_cap > 0 ? opt->history_cap : (int64_t)1 << 20;
+  cudaGetDevice(&ctx->device);
+  auto die = [&](int code, const std::string &msg) {
+    g_init_error = msg;
+    pdn_destroy(ctx);
+    return code;
+  };
+
+  // --- set-up on the host: lumped mass, lengths, stable steps -------------
+  std::vector<double> mass(nn, 0.0);
+  std::vector<double> vol(nh);
+  double cmax = 0.0;
+  {
+    Mat<double> tmp{};
+    std::string why;
+    int rc = fill_mat(tmp, m, mesh->ply_angle_deg, mesh->n_plies, opt->damage_on, opt->plasticity_on, why);
+    if (rc) return die(rc, why);
+    const double Cv[] = {tmp.C11, tmp.C12, tmp.C13, tmp.C22, tmp.C23, tmp.C33, tmp.G12, tmp.G13, tmp.G23};
+    for (double c : Cv) cmax = std::max(cmax, std::fabs(c));
+  }
+  double dtb = INFINITY;
+  const double sqrho = std::sqrt(m.rho / cmax);
+  for (int64_t e = 0; e < nh; ++e) {
+    double Xe[8][3], detJ[8], N[8][8];
+    for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < 3; ++i) Xe[a][i] = mesh->X[i * nn + mesh->hex[e * 8 + a]];
+    hex_gauss(Xe, detJ, N);
+    double V = 0.0;
+    for (int g = 0; g < 8; ++g) {
+      if (!(detJ[g] > 0)) return die(PDN_E_ARG, "hex with non-positive Jacobian (element " + std::to_string(e) + ")");
+      V += detJ[g];
+      for (int a = 0; a < 8; ++a) mass[mesh->hex[e * 8 + a]] += m.rho * N[g][a] * detJ[g];
+    }
+    vol[e] = V;
+    const double lc = std::cbrt(V);
+    dtb = std::min(dtb, lc * sqrho);
+    if (opt->damage_on) {
+      // crack-band limit of the softening laws (2 E G > lc X^2), with the
+      // largest seeded strengths
+      const double f = 1.0 + m.spread;
+      const double chk[5][3] = {{m.E1, m.GXT, m.XT * f}, {m.E1, m.GXC, m.XC}, {m.E2, m.GYT, m.YT * f},
+                                {m.E2, m.GYC, m.YC}, {m.G12, m.GSL, m.SL * f}};
+      for (auto &c : chk)
+        if (!(2.0 * c[0] * c[1] > lc * c[2] * c[2]))
+          return die(PDN_E_UNSTABLE, "element too large for the crack-band softening law (2 E G <= lc X^2)");
+    }
+  }
+  // node -> element-force slot CSR (hexes ascending, then interfaces ascending)
+  std::vector<int32_t> row(nn + 1, 0), col((size_t)(nh + nc) * 8);
+  for (int64_t k = 0; k < nh * 8; ++k) row[mesh->hex[k] + 1]++;
+  for (int64_t k = 0; k < nc * 8; ++k) row[mesh->coh[k] + 1]++;
+  for (int64_t j = 0; j < nn; ++j) row[j + 1] += row[j];
+  {
+    std::vector<int32_t> fill(row.begin(), row.end() - 1);
+    for (int64_t e = 0; e < nh; ++e)
+      for (int a = 0; a < 8; ++a) col[fill[mesh->hex[e * 8 + a]]++] = (int32_t)(e * 8 + a);
+    for (int64_t c = 0; c < nc; ++c)
+      for (int a = 0; a < 8; ++a) col[fill[mesh->coh[c * 8 + a]]++] = (int32_t)((nh + c) * 8 + a);
+  }
+  // interface stable step: rho_bar = rho * h, h = volume / face area of the
+  // thinner hex sharing a face with the interface element
+  double dtc = INFINITY;
+  for (int64_t c = 0; c < nc; ++c) {
+    double hmin = INFINITY;
+    for (int side = 0; side < 2; ++side) {
+      const int32_t *fn = mesh->coh + c * 8 + side * 4;
+      for (int32_t r = row[fn[0]]; r < row[fn[0] + 1]; ++r) {
+        const int32_t slot = col[r];
+        if (slot >= nh * 8) break;
+        const int64_t e = slot / 8;
+        int hit = 0;
+        for (int k = 0; k < 4; ++k)
+          for (int a = 0; a < 8; ++a)
+            if (mesh->hex[e * 8 + a] == fn[k]) {
+              ++hit;
+              break;
+            }
+        if (hit != 4) continue;
+        double p[4][3];
+        for (int k = 0; k < 4; ++k)
+          for (int i = 0; i < 3; ++i) p[k][i] = mesh->X[i * nn + fn[k]];
+        double u1[3], u2[3];
+        for (int i = 0; i < 3; ++i) {
+          u1[i] = p[2][i] - p[0][i];
+          u2[i] = p[3][i] - p[1][i];
+        }
+        const double cr0 = u1[1] * u2[2] - u1[2] * u2[1], cr1 = u1[2] * u2[0] - u1[0] * u2[2],
+                     cr2 = u1[0] * u2[1] - u1[1] * u2[0];
+        const double A = 0.5 * std::sqrt(cr0 * cr0 + cr1 * cr1 + cr2 * cr2);
+        hmin = std::min(hmin, vol[e] / A);
+      }
+    }
+    if (std::isfinite(hmin)) dtc = std::min(dtc, std::sqrt(m.rho * hmin / m.KI));
+  }
+  ctx->dt_bulk = dtb;
+  ctx->dt_coh = dtc;
+  const double safety = opt->dt_safety > 0 ? opt->dt_safety : 0.5;
+  ctx->dt = opt->dt > 0 ? opt->dt : safety * std::min(dtb, dtc);
+  if (!(ctx->dt > 0) || !std::isfinite(ctx->dt)) return die(PDN_E_UNSTABLE, "no finite stable time step");
+  for (int64_t j = 0; j < nn; ++j)
+    if (!(mass[j] > 0)) return die(PDN_E_ARG, "node " + std::to_string(j) + " has no mass (not in any hex)");
+
+  // --- device arena ---------------------------------------------------------
+  const bool fp64 = ctx->precision == PDN_FP64;
+  const size_t ts = fp64 ? 8 : 4;
+  const int n_part = grid_of(nn, kGatherBlock);
+  struct Ptrs {
+    int32_t *hex, *coh, *surf, *surf_of, *row, *col;
+    int8_t *ply;
+    char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
+    uint8_t *nflag, *act[2], *rel;
+    double *Xs, *mass, *d[2], *v[2], *nrm, *lam, *trial, *fhist, *fout;
+    Partial *part;
+    Ctl *ctl;
+    Striker *imp;
+    StrikerStep *imp_step;
+    float *field;
+  } P{};
+  const int64_t ns1 = std::max<int64_t>(ns, 1), nc1 = std::max<int64_t>(nc, 1);
+  // One layout function for both the sizing pass (base == nullptr) and the
+  // real pass, so the two cannot diverge.
+  auto layout = [&](Arena &A) {
+    P.hex = A.take<int32_t>(sizeof(int32_t) * nh * 8);
+    P.coh = A.take<int32_t>(sizeof(int32_t) * nc1 * 8);
+    P.ply = A.take<int8_t>(nh);
+    P.X4 = A.take<char>(ts * 4 * nn);
+    P.nflag = A.take<uint8_t>(nn);
+    P.surf = A.take<int32_t>(sizeof(int32_t) * ns1);
+    P.surf_of = A.take<int32_t>(sizeof(int32_t) * nn);
+    P.Xs = A.take<double>(sizeof(double) * 3 * ns1);
+    P.row = A.take<int32_t>(sizeof(int32_t) * (nn + 1));
+    P.col = A.take<int32_t>(sizeof(int32_t) * (nh + nc) * 8);
+    P.mass = A.take<double>(sizeof(double) * nn);
+    P.imass = A.take<char>(ts * nn);
+    for (int b = 0; b < 2; ++b) {
+      P.d[b] = A.take<double>(sizeof(double) * 3 * nn);
+      P.v[b] = A.take<double>(sizeof(double) * 3 * nn);
+      P.u4[b] = A.take<char>(ts * 4 * nn);
+      P.hist[b] = A.take<char>(ts * 7 * 8 * nh);
+      P.rD[b] = A.take<char>(ts * 4 * nc1);
+      P.act[b] = A.take<uint8_t>(ns1);
+    }
+    P.fe = A.take<char>(ts * 4 * (nh + nc) * 8);
+    P.rel = A.take<uint8_t>(ns1);
+    P.nrm = A.take<double>(sizeof(double) * 3 * ns1);
+    P.lam = A.take<double>(sizeof(double) * ns1);
+    P.trial = A.take<double>(sizeof(double) * 6 * ns1);
+    P.part = A.take<Partial>(sizeof(Partial) * n_part);
+    P.ctl = A.take<Ctl>(sizeof(Ctl));
+    P.imp = A.take<Striker>(sizeof(Striker));
+    P.imp_step = A.take<StrikerStep>(sizeof(StrikerStep));
+    P.fhist = A.take<double>(sizeof(double) * ctx->hist_cap);
+    P.fout = A.take<double>(sizeof(double) * 3 * nn);
+    P.field = A.take<float>(sizeof(float) * std::max(nh, nc1));
+  };
+  Arena probe;
+  layout(probe);
+  cudaError_t ce = cudaMalloc(&ctx->arena.base, probe.used);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    return die(PDN_E_OOM, std::string("device allocation of ") + std::to_string(probe.used) + " bytes failed: " +
+                              cudaGetErrorString(ce));
+  }
+  ctx->arena.size = probe.used;
+  ctx->arena.used = 0;
+  layout(ctx->arena);
+  int32_t *d_hex = P.hex, *d_coh = P.coh, *d_surf = P.surf, *d_surf_of = P.surf_of, *d_row = P.row, *d_col = P.col;
+  int8_t *d_ply = P.ply;
+  char *d_X4 = P.X4, *d_imass = P.imass, *d_fe = P.fe;
+  uint8_t *d_nflag = P.nflag, *d_rel = P.rel;
+  double *d_Xs = P.Xs, *d_mass = P.mass, *d_nrm = P.nrm, *d_lam = P.lam, *d_trial = P.trial, *d_fhist = P.fhist,
+         *d_fout = P.fout;
+  double *d_d[2] = {P.d[0], P.d[1]}, *d_v[2] = {P.v[0], P.v[1]};
+  char *d_u4[2] = {P.u4[0], P.u4[1]}, *d_hist[2] = {P.hist[0], P.hist[1]}, *d_rD[2] = {P.rD[0], P.rD[1]};
+  uint8_t *d_act[2] = {P.act[0], P.act[1]};
+  Partial *d_part = P.part;
+  ctx->ctl_dev = P.ctl;
+  ctx->imp_dev = P.imp;
+  StrikerStep *d_imp_step = P.imp_step;
+  ctx->field = P.field;
+
+  if (opt->stream) {
+    ctx->stream = (cudaStream_t)opt->stream;
+  } else {
+    ce = cudaStreamCreate(&ctx->stream);  // blocking: ordered with the legacy default stream
+    if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("stream create: ") + cudaGetErrorString(ce));
+    ctx->own_stream = true;
+  }
+  ce = cudaMallocHost(&ctx->ctl_host, sizeof(Ctl));
+  if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("pinned allocation: ") + cudaGetErrorString(ce));
+
+  // host-side staging of the uploads
+  std::vector<uint8_t> nflag(nn, 0);
+  for (int64_t j = 0; j < nn; ++j) {
+    nflag[j] = mesh->fixed ? mesh->fixed[j] : 0;
+    if (surf_of[j] >= 0) nflag[j] |= 8;
+  }
+  std::vector<double> Xs(3 * std::max<int64_t>(ns, 1), 0.0);
+  for (int64_t s = 0; s < ns; ++s)
+    for (int i = 0; i < 3; ++i) Xs[i * ns + s] = mesh->X[i * nn + mesh->surf[s]];
+  std::vector<char> X4(ts * 4 * nn), imass(ts * nn);
+  for (int64_t j = 0; j < nn; ++j) {
+    if (fp64) {
+      double *q = reinterpret_cast<double *>(X4.data()) + 4 * j;
+      q[0] = mesh->X[j];
+      q[1] = mesh->X[nn + j];
+      q[2] = mesh->X[2 * nn + j];
+      q[3] = 0.0;
+      reinterpret_cast<double *>(imass.data())[j] = 1.0 / mass[j];
+    } else {
+      float *q = reinterpret_cast<float *>(X4.data()) + 4 * j;
+      q[0] = (float)mesh->X[j];
+      q[1] = (float)mesh->X[nn + j];
+      q[2] = (float)mesh->X[2 * nn + j];
+      q[3] = 0.0f;
+      reinterpret_cast<float *>(imass.data())[j] = (float)(1.0 / mass[j]);
+    }
+  }
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(up(d_hex, mesh->hex, sizeof(int32_t) * nh * 8));
+  if (nc) chk(up(d_coh, mesh->coh, sizeof(int32_t) * nc * 8));
+  chk(up(d_ply, mesh->ply_of_hex, nh));
+  chk(up(d_X4, X4.data(), X4.size()));
+  chk(up(d_nflag, nflag.data(), nn));
+  if (ns) chk(up(d_surf, mesh->surf, sizeof(int32_t) * ns));
+  chk(up(d_surf_of, surf_of.data(), sizeof(int32_t) * nn));
+  chk(up(d_Xs, Xs.data(), sizeof(double) * Xs.size()));
+  chk(up(d_row, row.data(), sizeof(int32_t) * (nn + 1)));
+  chk(up(d_col, col.data(), sizeof(int32_t) * col.size()));
+  chk(up(d_mass, mass.data(), sizeof(double) * nn));
+  chk(up(d_imass, imass.data(), imass.size()));
+  for (int b = 0; b < 2; ++b) {
+    chk(cudaMemset(d_d[b], 0, sizeof(double) * 3 * nn));
+    chk(cudaMemset(d_v[b], 0, sizeof(double) * 3 * nn));
+    chk(cudaMemset(d_u4[b], 0, ts * 4 * nn));
+    chk(cudaMemset(d_rD[b], 0, ts * 4 * std::max<int64_t>(nc, 1)));
+    chk(cudaMemset(d_act[b], 0, std::max<int64_t>(ns, 1)));
+    if (fp64)
+      k_fill_hist_double<<<grid_of(nh * 8 * 7, 256), 256>>>(reinterpret_cast<double *>(d_hist[b]), nh * 8, 4);
+    else
+      k_fill_hist_float<<<grid_of(nh * 8 * 7, 256), 256>>>(reinterpret_cast<float *>(d_hist[b]), nh * 8, 4);
+    chk(cudaGetLastError());
+  }
+  chk(cudaMemset(d_fe, 0, ts * 4 * (nh + nc) * 8));
+  chk(cudaMemset(d_rel, 0, std::max<int64_t>(ns, 1)));
+  chk(cudaMemset(d_nrm, 0, sizeof(double) * 3 * std::max<int64_t>(ns, 1)));
+  chk(cudaMemset(d_lam, 0, sizeof(double) * std::max<int64_t>(ns, 1)));
+  chk(cudaMemset(d_part, 0, sizeof(Partial) * n_part));
+  Ctl c0{};
+  c0.mode = MODE_DONE;
+  c0.max_repeats = ctx->max_repeats;
+  chk(up(ctx->ctl_dev, &c0, sizeof(Ctl)));
+  Striker s0{};
+  s0.axis[2] = -1.0;
+  s0.M = 1.0;
+  for (int i = 0; i < 3; ++i) s0.g[i] = ctx->grav[i];
+  chk(up(ctx->imp_dev, &s0, sizeof(Striker)));
+  chk(cudaMemset(d_imp_step, 0, sizeof(StrikerStep)));
+  chk(cudaDeviceSynchronize());
+  if (e != cudaSuccess) return die(PDN_E_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+
+  std::string why;
+  int rc = fill_mat(ctx->Mf, m, mesh->ply_angle_deg, mesh->n_plies, opt->damage_on, opt->plasticity_on, why);
+  if (!rc) rc = fill_mat(ctx->Md, m, mesh->ply_angle_deg, mesh->n_plies, opt->damage_on, opt->plasticity_on, why);
+  if (rc) return die(rc, why);
+
+  auto wire = [&](auto &D, auto tag) {
+    using T = decltype(tag);
+    using V4 = typename Vec4T<T>::type;
+    D.nn = nn;
+    D.nh = nh;
+    D.nc = nc;
+    D.ns = ns;
+    D.hex = d_hex;
+    D.coh = d_coh;
+    D.ply = d_ply;
+    D.X4 = reinterpret_cast<const V4 *>(d_X4);
+    D.nflag = d_nflag;
+    D.surf = d_surf;
+    D.surf_of = d_surf_of;
+    D.Xs = d_Xs;
+    D.row = d_row;
+    D.col = d_col;
+    D.mass = d_mass;
+    D.inv_mass = reinterpret_cast<const T *>(d_imass);
+    for (int b = 0; b < 2; ++b) {
+      D.d[b] = d_d[b];
+      D.v[b] = d_v[b];
+      D.u4[b] = reinterpret_cast<V4 *>(d_u4[b]);
+      D.hist[b] = reinterpret_cast<T *>(d_hist[b]);
+      D.rD[b] = reinterpret_cast<T *>(d_rD[b]);
+      D.act[b] = d_act[b];
+    }
+    D.fe = reinterpret_cast<V4 *>(d_fe);
+    D.rel = d_rel;
+    D.nrm = d_nrm;
+    D.lam = d_lam;
+    D.trial = d_trial;
+    D.part = d_part;
+    D.n_part = n_part;
+    D.ctl = ctx->ctl_dev;
+    D.imp = ctx->imp_dev;
+    D.imp_step = d_imp_step;
+    D.fhist = d_fhist;
+    D.hist_cap = ctx->hist_cap;
+    D.fout = d_fout;
+    D.dt = ctx->dt;
+    D.phi = ctx->phi;
+    for (int i = 0; i < 3; ++i) D.grav[i] = ctx->grav[i];
+  };
+  if (fp64)
+    wire(ctx->Dd, double{});
+  else
+    wire(ctx->Df, float{});
+  *out = ctx;
+  return PDN_OK;
+}
+
+int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double centre[3], const double velocity[3]) {
+  if (!ctx) return PDN_E_ARG;
+  if (!centre || !velocity || !(radius > 0) || !(mass > 0)) return fail(ctx, PDN_E_ARG, "radius and mass must be positive");
+  Striker s{};
+  const double n = std::sqrt(velocity[0] * velocity[0] + velocity[1] * velocity[1] + velocity[2] * velocity[2]);
+  for (int i = 0; i < 3; ++i) {
+    s.c[i] = centre[i];
+    s.w[i] = velocity[i];
+    s.F[i] = 0.0;
+    s.axis[i] = n > 0 ? velocity[i] / n : (i == 2 ? -1.0 : 0.0);
+    s.g[i] = ctx->grav[i];
+  }
+  s.R = radius;
+  s.M = mass;
+  s.has = 1;
+  PDN_CU(cudaMemcpyAsync(ctx->imp_dev, &s, sizeof(Striker), cudaMemcpyHostToDevice, ctx->stream), "set impactor");
+  PDN_CU(cudaStreamSynchronize(ctx->stream), "set impactor");
+  ctx->has_imp = true;
+  return PDN_OK;
+}
+
+int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
+  if (!ctx) return PDN_E_ARG;
+  if (nsteps < 0) return fail(ctx, PDN_E_ARG, "nsteps < 0");
+  if (!ctx->has_imp) return fail(ctx, PDN_E_STATE, "pdn_set_impactor must be called before pdn_step");
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "device halted earlier (sticky status)");
+  if (nsteps == 0) return PDN_OK;
+  const int64_t target = ctx->ctl_host->step + nsteps;
+  rc = set_mode(ctx, MODE_ADVANCE, target);
+  if (rc) return rc;
+  int64_t remaining = nsteps;
+  for (int guard = 0; remaining > 0; ++guard) {
+    cudaError_t e = launch_passes(ctx, remaining);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch step passes");
+    rc = read_ctl(ctx);
+    if (rc) return rc;
+    const Ctl &c = *ctx->ctl_host;
+    if (c.status) {
+      return fail(ctx, c.status, c.status == PDN_E_NONFINITE ? "non-finite acceleration or displacement"
+                                                             : "contact release limit reached (Algorithm 2)");
+    }
+    remaining = target - c.step;
+    if (guard > 64 * (ctx->max_repeats + 1)) return fail(ctx, PDN_E_STATE, "step loop made no progress");
+  }
+  return PDN_OK;
+}
+
+int pdn_profile_kernels(pdn_ctx *ctx, int64_t nsteps, float *ms_per_launch, int64_t *launches) {
+  if (!ctx) return PDN_E_ARG;
+  if (nsteps < 0) return fail(ctx, PDN_E_ARG, "nsteps < 0");
+  if (!ctx->has_imp) return fail(ctx, PDN_E_STATE, "pdn_set_impactor must be called first");
+  if (ctx->prof_ev.empty()) {
+    ctx->prof_ev.resize(6 * kProfilePasses);
+    for (auto &e : ctx->prof_ev) PDN_CU(cudaEventCreate(&e), "event create");
+  }
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "device halted earlier (sticky status)");
+  const int64_t target = ctx->ctl_host->step + nsteps;
+  rc = set_mode(ctx, MODE_ADVANCE, target);
+  if (rc) return rc;
+  double tot[PDN_K_COUNT] = {0};
+  int64_t cnt[PDN_K_COUNT] = {0};
+  int64_t remaining = nsteps;
+  while (remaining > 0) {
+    const int64_t chunk = std::min<int64_t>(remaining, kProfilePasses);
+    for (int64_t p = 0; p < chunk; ++p) {
+      cudaError_t e = run_pass(ctx, ctx->prof_ev.data() + 6 * p);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "profile pass");
+    }
+    rc = read_ctl(ctx);
+    if (rc) return rc;
+    for (int64_t p = 0; p < chunk; ++p)
+      for (int k = 0; k < PDN_K_COUNT; ++k) {
+        if (k == PDN_K_COH && ctx->nc == 0) continue;
+        float ms = 0.f;
+        PDN_CU(cudaEventElapsedTime(&ms, ctx->prof_ev[6 * p + k], ctx->prof_ev[6 * p + k + 1]), "event time");
+        tot[k] += ms;
+        cnt[k] += 1;
+      }
+    const Ctl &c = *ctx->ctl_host;
+    if (c.status) return fail(ctx, c.status, "device halted during profiling");
+    remaining = target - c.step;
+  }
+  for (int k = 0; k < PDN_K_COUNT; ++k) {
+    if (ms_per_launch) ms_per_launch[k] = cnt[k] ? (float)(tot[k] / cnt[k]) : 0.f;
+    if (launches) launches[k] = cnt[k];
+  }
+  return PDN_OK;
+}
+
+int64_t pdn_contact_force(pdn_ctx *ctx, double f_now[3], double *f_peak, double *history, int64_t cap) {
+  if (!ctx) return PDN_E_ARG;
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (f_now) {
+    Striker s;
+    PDN_CU(cudaMemcpy(&s, ctx->imp_dev, sizeof(Striker), cudaMemcpyDeviceToHost), "read striker");
+    for (int i = 0; i < 3; ++i) f_now[i] = s.F[i];
+  }
+  if (f_peak) *f_peak = ctx->ctl_host->f_peak;
+  int64_t n = std::min<int64_t>(ctx->ctl_host->hist_count, cap > 0 ? cap : 0);
+  if (history && n > 0) {
+    const double *src = ctx->precision == PDN_FP64 ? ctx->Dd.fhist : ctx->Df.fhist;
+    PDN_CU(cudaMemcpy(history, src, sizeof(double) * n, cudaMemcpyDeviceToHost), "read force history");
+  }
+  return history ? n : ctx->ctl_host->hist_count;
+}
+
+int pdn_damage_field(pdn_ctx *ctx, int32_t which, float *out, int64_t n, int32_t out_on_device) {
+  if (!ctx) return PDN_E_ARG;
+  if (which < PDN_FIELD_D1 || which > PDN_FIELD_PLASTIC) return fail(ctx, PDN_E_ARG, "unknown field");
+  const int64_t need = which == PDN_FIELD_DCOH ? ctx->nc : ctx->nh;
+  if (!out || n != need) return fail(ctx, PDN_E_ARG, "output size must equal the element count of the field");
+  if (need == 0) return PDN_OK;
+  cudaError_t e = ctx->precision == PDN_FP64 ? launch_damage_field<double>(ctx->Dd, ctx->Md, which, ctx->field, ctx->stream)
+                                             : launch_damage_field<float>(ctx->Df, ctx->Mf, which, ctx->field, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "damage field kernel");
+  PDN_CU(cudaMemcpyAsync(out, ctx->field, sizeof(float) * n,
+                         out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream),
+         "copy damage field");
+  PDN_CU(cudaStreamSynchronize(ctx->stream), "damage field");
+  return PDN_OK;
+}
+
+int pdn_get_state(pdn_ctx *ctx, double *d, double *v, double *imp) {
+  if (!ctx) return PDN_E_ARG;
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  const int b = ctx->ctl_host->dpar ^ 1;
+  double *const *dd = ctx->precision == PDN_FP64 ? ctx->Dd.d : ctx->Df.d;
+  double *const *vv = ctx->precision == PDN_FP64 ? ctx->Dd.v : ctx->Df.v;
+  if (d) PDN_CU(cudaMemcpy(d, dd[b], sizeof(double) * 3 * ctx->nn, cudaMemcpyDeviceToHost), "read d");
+  if (v) PDN_CU(cudaMemcpy(v, vv[b], sizeof(double) * 3 * ctx->nn, cudaMemcpyDeviceToHost), "read v");
+  if (imp) {
+    Striker s;
+    PDN_CU(cudaMemcpy(&s, ctx->imp_dev, sizeof(Striker), cudaMemcpyDeviceToHost), "read striker");
+    for (int i = 0; i < 3; ++i) {
+      imp[i] = s.c[i];
+      imp[3 + i] = s.w[i];
+      imp[6 + i] = s.F[i];
+    }
+    imp[9] = ctx->ctl_host->time;
+  }
+  return PDN_OK;
+}
+
+int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v) {
+  if (!ctx) return PDN_E_ARG;
+  if (!d || !v) return fail(ctx, PDN_E_ARG, "d and v are required");
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "device halted earlier (sticky status)");
+  const int b = ctx->ctl_host->dpar;
+  const int64_t nn = ctx->nn;
+  std::vector<uint8_t> nflag(nn);
+  const uint8_t *fl = ctx->precision == PDN_FP64 ? ctx->Dd.nflag : ctx->Df.nflag;
+  PDN_CU(cudaMemcpy(nflag.data(), fl, nn, cudaMemcpyDeviceToHost), "read flags");
+  std::vector<double> dh(d, d + 3 * nn), vh(v, v + 3 * nn);
+  for (int64_t j = 0; j < nn; ++j)
+    for (int i = 0; i < 3; ++i)
+      if ((nflag[j] >> i) & 1) {
+        dh[i * nn + j] = 0.0;
+        vh[i * nn + j] = 0.0;
+      }
+  double *const *dd = ctx->precision == PDN_FP64 ? ctx->Dd.d : ctx->Df.d;
+  double *const *vv = ctx->precision == PDN_FP64 ? ctx->Dd.v : ctx->Df.v;
+  PDN_CU(cudaMemcpy(dd[b], dh.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice), "write d");
+  PDN_CU(cudaMemcpy(vv[b], vh.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice), "write v");
+  if (ctx->precision == PDN_FP64)
+    k_mirror<double4_32a><<<grid_of(nn, 256), 256, 0, ctx->stream>>>(dd[b], ctx->Dd.u4[b], nn);
+  else
+    k_mirror<float4><<<grid_of(nn, 256), 256, 0, ctx->stream>>>(dd[b], ctx->Df.u4[b], nn);
+  PDN_CU(cudaGetLastError(), "mirror kernel");
+  rc = set_mode(ctx, MODE_PRIME, ctx->ctl_host->step);
+  if (rc) return rc;
+  cudaError_t e = run_pass(ctx, nullptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "prime pass");
+  rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "non-finite state installed");
+  return PDN_OK;
+}
+
+int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {
+  if (!ctx) return PDN_E_ARG;
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  const int64_t ns = ctx->ns;
+  if (ns == 0) return PDN_OK;
+  const int par = (int)(ctx->ctl_host->step & 1);
+  uint8_t *const *act = ctx->precision == PDN_FP64 ? ctx->Dd.act : ctx->Df.act;
+  const double *lam = ctx->precision == PDN_FP64 ? ctx->Dd.lam : ctx->Df.lam;
+  std::vector<uint8_t> a(ns);
+  PDN_CU(cudaMemcpy(a.data(), act[par], ns, cudaMemcpyDeviceToHost), "read contact set");
+  if (active) std::memcpy(active, a.data(), ns);
+  if (lambda) {
+    PDN_CU(cudaMemcpy(lambda, lam, sizeof(double) * ns, cudaMemcpyDeviceToHost), "read reactions");
+    for (int64_t s = 0; s < ns; ++s)
+      if (!a[s]) lambda[s] = 0.0;
+  }
+  return PDN_OK;
+}
+
+int pdn_internal_force(pdn_ctx *ctx, double *f_int) {
+  if (!ctx) return PDN_E_ARG;
+  if (!f_int) return fail(ctx, PDN_E_ARG, "f_int is NULL");
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "device halted earlier (sticky status)");
+  rc = set_mode(ctx, MODE_FORCES, ctx->ctl_host->step);
+  if (rc) return rc;
+  cudaError_t e = run_pass(ctx, nullptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "force pass");
+  const double *fo = ctx->precision == PDN_FP64 ? ctx->Dd.fout : ctx->Df.fout;
+  PDN_CU(cudaMemcpyAsync(f_int, fo, sizeof(double) * 3 * ctx->nn, cudaMemcpyDeviceToHost, ctx->stream), "read forces");
+  PDN_CU(cudaStreamSynchronize(ctx->stream), "force pass");
+  return PDN_OK;
+}
+
+int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
+  if (!ctx || !info) return PDN_E_ARG;
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  const Ctl &c = *ctx->ctl_host;
+  info->dt = ctx->dt;
+  info->dt_bulk = ctx->dt_bulk;
+  info->dt_coh = ctx->dt_coh;
+  info->time = c.time;
+  info->f_peak = c.f_peak;
+  info->step = c.step;
+  info->n_active = c.n_active;
+  info->n_repeats = c.n_repeats_total;
+  info->n_nodes = ctx->nn;
+  info->n_hex = ctx->nh;
+  info->n_coh = ctx->nc;
+  info->n_surf = ctx->ns;
+  info->device_bytes = (int64_t)ctx->arena.size;
+  info->status = c.status;
+  info->precision = ctx->precision;
+  return PDN_OK;
+}
+
+}  // extern "C"

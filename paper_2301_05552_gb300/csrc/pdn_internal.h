@@ -1,0 +1,149 @@
+// Internal records shared by the kernel and host translation units of the
+// GB300 explicit PDN impact step.  Not part of the public C ABI (pdn.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pdn {
+
+// Device-side state machine of a pass.  A pass is one launch of the five step
+// kernels (contact, hex, interface, gather, tail); the tail decides whether
+// the next pass advances to a new step or repeats the current one after
+// releasing adhesive contact nodes (Algorithm 2).
+enum Mode : int32_t {
+  MODE_ADVANCE = 0,  // next pass computes a new step
+  MODE_REPEAT = 1,   // next pass repeats the current step with released nodes
+  MODE_PRIME = 2,    // next pass recomputes the acceleration of an installed state
+  MODE_FORCES = 3,   // next pass evaluates internal forces of the committed state
+  MODE_DONE = 4,     // target step reached: passes are no-ops
+  MODE_HALT = 5      // sticky error: passes are no-ops
+};
+
+struct Ctl {
+  int32_t mode;
+  int32_t dpar;        // node buffer holding the current pass's displacement
+  int32_t hpar;        // history buffer holding the committed history
+  int32_t repeats;     // repetitions of the current step so far
+  int32_t status;      // 0 or a PDN_E_* code
+  int32_t max_repeats;
+  int64_t step;        // committed steps
+  int64_t target;      // step at which passes stop
+  int64_t n_active;    // contact nodes of the last committed step
+  int64_t n_repeats_total;
+  int64_t hist_count;  // contact-force samples written
+  double time;
+  double f_peak;
+};
+
+// Rigid striker (Sec. 2.2.2).  The committed part is written only by the tail
+// kernel; every pass recomputes the step-(n+1) state from it.
+struct Striker {
+  double c[3], w[3];  // centre and velocity at the committed step n
+  double F[3];        // contact force on the plate at step n: sum_j lambda_j n_j
+  double axis[3];     // unit impact direction (the only free degree of freedom)
+  double R, M;
+  double g[3];
+  int32_t has;
+  int32_t pad;
+};
+
+// Striker state of the step being computed (n+1) and the acceleration used
+// over it; written by the contact kernel, read by gather and tail.
+struct StrikerStep {
+  double c[3], w[3], aI[3];
+};
+
+// Per-block partial results of the gather (deterministic second-pass sum).
+struct Partial {
+  double f[3];
+  int32_t n_act, n_adh, nonfinite, pad;
+};
+
+constexpr int kMaxPlies = 64;
+
+// Material constants in the element precision T (computed once on the host).
+template <typename T>
+struct Mat {
+  // undamaged stiffness (ply axes, Voigt 11 22 33 12 13 23)
+  T C11, C12, C13, C22, C23, C33, G12, G13, G23;
+  // undamaged compliance, normal block
+  T h11, h22, h33, h12, h13, h23;
+  T E1, E2;
+  T XT, XC, YT, YC, SL;
+  T GXT, GXC, GYT, GYC, GSL;
+  T ca, sa, etaT, ST, etaLc;  // fracture-plane constants; etaL = SL * etaLc
+  T g;                        // GYT / GSL
+  T Sp, Kp;
+  // interface
+  T KI, Ksh, KI_D3o2, Ksh_Dsho2, KI_D3oD3c, Ksh_DshoDshc, eta, onset_floor;
+  T spread;
+  T ply_c[kMaxPlies], ply_s[kMaxPlies];
+  uint64_t seed;
+  int32_t damage_on, plasticity_on;
+};
+
+template <typename T>
+struct Vec4T;
+template <>
+struct Vec4T<float> {
+  using type = float4;
+};
+template <>
+struct Vec4T<double> {
+  using type = double4_32a;  // 32-byte aligned: one 256-bit access per node
+};
+
+// Pointers of a context's device state for the step kernels.
+template <typename T>
+struct Dev {
+  using V4 = typename Vec4T<T>::type;
+  int64_t nn, nh, nc, ns;
+  // mesh
+  const int32_t *hex;      // [nh][8]
+  const int32_t *coh;      // [nc][8]
+  const int8_t *ply;       // [nh]
+  const V4 *X4;            // [nn] reference coordinates (x, y, z, 0) in T
+  const uint8_t *nflag;    // [nn] bits 0-2 constraint, bit 3 contact surface
+  const int32_t *surf;     // [ns]
+  const int32_t *surf_of;  // [nn] surface index or -1
+  const double *Xs;        // [3][ns] surface reference coordinates (FP64)
+  const int32_t *row;      // [nn + 1] CSR of node -> element-force slot
+  const int32_t *col;      // [nnz] slot = 8*e + k (hex), 8*(nh + c) + k (interface)
+  const double *mass;      // [nn]
+  const T *inv_mass;       // [nn]
+  // state (double buffered)
+  double *d[2], *v[2];     // [3][nn]
+  V4 *u4[2];               // [nn] element-precision mirror of d
+  T *hist[2];              // [7][8][nh] history per Gauss point
+  T *rD[2];                // [4][nc] interface thresholds
+  V4 *fe;                  // [(nh + nc) * 8] element nodal forces
+  // contact
+  uint8_t *act[2];         // [ns] contact set by step parity
+  uint8_t *rel;            // [ns] released in the current step
+  double *nrm;             // [3][ns]
+  double *lam;             // [ns]
+  double *trial;           // [6][ns] pre-projection d and v of active nodes
+  // reductions and control
+  Partial *part;           // [gather blocks]
+  int32_t n_part;
+  Ctl *ctl;
+  Striker *imp;
+  StrikerStep *imp_step;
+  double *fhist;           // [hist_cap]
+  int64_t hist_cap;
+  double *fout;            // [3][nn] internal force output (MODE_FORCES)
+  // integration
+  double dt, phi;
+  double grav[3];
+};
+
+// Launchers (pdn_kernels.cu).
+template <typename T>
+cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_t gather_block,
+                        cudaEvent_t *ev /* [2 * 5] or nullptr */);
+template <typename T>
+cudaError_t launch_damage_field(const Dev<T> &D, const Mat<T> &M, int which, float *out,
+                                cudaStream_t s);
+
+}  // namespace pdn

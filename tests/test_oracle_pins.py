@@ -564,3 +564,44 @@ def test_material_constants_follow_table1():
         assert m[k] == tab[k]
     a0 = math.radians(tab["alpha0_deg"])
     assert m["GYC"] == pytest.approx(m["GSL"] / math.cos(a0), rel=1e-14)  # Table 1 note b
+
+
+@pytest.mark.slow
+def test_hertz_impact_on_elastic_block():
+    """Rigid sphere (R = 25 mm) on an isotropic block at low speed (v/c ~ 1.6e-3):
+    peak indentation and force against Hertz's impact solution
+    delta_max = (15 M v^2 / (16 E* sqrt(R)))^(2/5), F_max = 4/3 E* sqrt(R) delta_max^(3/2),
+    and the loading branch F ~ delta^(3/2).  Quarter-symmetry block 12.5 mm
+    (x = 0, y = 0 symmetry planes, base clamped), 0.5 mm elements, contact
+    radius 2.5 mm = 5 elements.  The finite clamped block is stiffer than the
+    half-space of the closed form (F +7.7 %, delta -4.2 % here; +5.7 % and
+    -3.3 % with a 15 mm block), hence 9 % / 6 % bounds."""
+    L = D = 12.5
+    h = 0.5
+    E, nu, rho, R, v = 1e4, 0.3, 1.6e-9, 25.0, 4000.0
+    n = int(round(L / h))
+    plate = pi.make_plate(L, L, D, n, n, [0.0], n, cohesive=False, clamp="quarter")
+    mat = pi.material_isotropic(E, nu, rho)
+    Es = E / (1 - nu ** 2)
+    M = (0.25 ** 2.5) * 16 * Es * math.sqrt(R) / 15 / v ** 2    # designed for delta_max = 0.25 mm
+    model = oracle.Model(plate, mat)
+    model.set_impactor(R, M / 4, (0.0, 0.0, D + R + 1e-4), (0.0, 0.0, -v))  # quarter of the striker
+    dt = model.info()["dt"]
+    nsteps = int(1.2 * 2.94 * 0.25 / v / dt)
+    z = []
+    for _ in range(nsteps // 25):
+        model.step(25)
+        z.append(model.impactor()["centre"][2])
+    F = 4.0 * model.force_history()
+    dmax_h = (15 * M * v ** 2 / (16 * Es * math.sqrt(R))) ** 0.4
+    Fmax_h = 4.0 / 3.0 * Es * math.sqrt(R) * dmax_h ** 1.5
+    delta_max = (D + R) - min(z)
+    assert delta_max == pytest.approx(dmax_h, rel=0.06)
+    assert F.max() == pytest.approx(Fmax_h, rel=0.09)
+    # loading branch: fit F = k delta^p between 30 % and 90 % of the peak
+    zs = np.interp(np.arange(len(F)), np.arange(25, 25 * len(z) + 1, 25) - 1, np.array(z))
+    delta = (D + R) - zs
+    k_peak = int(np.argmax(F))
+    sel = (F[:k_peak] > 0.3 * F.max()) & (F[:k_peak] < 0.9 * F.max()) & (delta[:k_peak] > 0)
+    p = np.polyfit(np.log(delta[:k_peak][sel]), np.log(F[:k_peak][sel]), 1)[0]
+    assert 1.35 < p < 1.65
