@@ -240,6 +240,51 @@ int pdn_profile_kernels(pdn_ctx *ctx, int64_t nsteps, float *ms_per_launch, int6
 /* Release all device memory of the context.  NULL is ignored. */
 void pdn_destroy(pdn_ctx *ctx);
 
+/* Largest mesh pdn_internal_force_noalloc accepts (its static scratch). */
+#define PDN_NOALLOC_MAX_HEX 8192
+#define PDN_NOALLOC_MAX_NODES 16384
+
+/* Nodal internal force of a hex8 mesh for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a library service.
+ *
+ * Who needs it: code that runs under a memory manager owning all device
+ * memory (a framework's caching allocator, a fixed device-memory budget)
+ * and must not call cudaMalloc/cudaFree itself, or that must avoid their
+ * implicit device synchronisation in steady state.  Such a caller cannot
+ * create a context (pdn_init_mesh allocates).  This call computes the same
+ * quantity as pdn_internal_force, with the same element and gather kernels,
+ * from caller buffers, and calls no allocating routine: its working memory
+ * (element forces, mirrors, trial history, partial sums, control block,
+ * about 10.5 MB) is a fixed array in device global memory that every device
+ * loading this library holds until the process exits.
+ *
+ * Device pointers (all caller-owned): hex [n_hex][8] and ply_of_hex [n_hex]
+ * as in pdn_mesh_desc (node ids in [0, n_nodes), ply ids in [0, n_plies));
+ * X and d [3][n_nodes] FP64; history [7][8][n_hex] in the element precision
+ * (float for PDN_FP32_FORCE, double for PDN_FP64: fields rFT rFC rMT rMC
+ * gp12 gp13 pbar per Gauss point), read only, or NULL for the undamaged
+ * state; csr_row [n_nodes+1] and csr_col [8 n_hex], the node -> element slot
+ * map: csr_col[csr_row[j] .. csr_row[j+1]) lists 8*e + k for every hex e
+ * whose local node k is j, in ascending order; f_int [3][n_nodes] output.
+ * Host pointers: mat, ply_angle_deg [n_plies].  stream is a cudaStream_t
+ * (NULL = legacy default stream); the call only enqueues work on it.
+ *
+ * Errors: PDN_E_ARG (message from pdn_last_error(NULL)) when n_hex exceeds
+ * PDN_NOALLOC_MAX_HEX, n_nodes exceeds PDN_NOALLOC_MAX_NODES, a pointer is
+ * NULL or a parameter is invalid; PDN_E_CUDA on a launch failure.  Device
+ * contents are not validated (out-of-range ids are the caller's fault).
+ *
+ * The first call on a device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array: calls
+ * whose work overlaps on the GPU (several streams or host threads on one
+ * device) race and must be serialised by the caller. */
+int pdn_internal_force_noalloc(int64_t n_nodes, int64_t n_hex, const int32_t *hex, const int8_t *ply_of_hex,
+                               const double *X, const double *d, const void *history, const int32_t *csr_row,
+                               const int32_t *csr_col, const pdn_material *mat, const double *ply_angle_deg,
+                               int32_t n_plies, int32_t precision, int32_t damage_on, int32_t plasticity_on,
+                               double *f_int, void *stream);
+
 /* Last error message of a context (never NULL); with ctx == NULL, the last
  * error of a failed pdn_init_mesh in this thread. */
 const char *pdn_last_error(const pdn_ctx *ctx);

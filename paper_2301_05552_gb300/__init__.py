@@ -37,7 +37,7 @@ ERRORS = {-1: "PDN_E_ARG", -2: "PDN_E_CUDA", -3: "PDN_E_OOM", -4: "PDN_E_NONFINI
           -5: "PDN_E_RELEASE_LIMIT", -6: "PDN_E_TIMEOUT", -7: "PDN_E_UNSTABLE", -8: "PDN_E_STATE"}
 EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
            "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
-           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error"]
+           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc"]
 
 
 class PdnError(RuntimeError):
@@ -112,6 +112,10 @@ def lib():
             L.pdn_destroy.restype = None
             L.pdn_last_error.argtypes = [vp]
             L.pdn_last_error.restype = C.c_char_p
+            L.pdn_internal_force_noalloc.argtypes = [C.c_int64, C.c_int64, vp, vp, vp, vp, vp, vp, vp,
+                                                     C.POINTER(Material), dp, C.c_int32, C.c_int32, C.c_int32,
+                                                     C.c_int32, vp, vp]
+            L.pdn_internal_force_noalloc.restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
                          "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
                          "pdn_init_mesh"):
@@ -293,6 +297,28 @@ def pdn_destroy(ctx: Context):
 
 def pdn_last_error(ctx: Optional[Context]) -> str:
     return (lib().pdn_last_error(ctx.handle if ctx is not None else None) or b"").decode()
+
+
+def pdn_internal_force_noalloc(n_nodes: int, n_hex: int, hex_dev, ply_dev, X_dev, d_dev, history_dev,
+                               row_dev, col_dev, material: dict, ply_angle_deg, precision: int,
+                               damage_on: bool, plasticity_on: bool, f_out_dev, stream: Optional[int] = None):
+    """pdn_internal_force_noalloc: every array argument is a CUDA tensor (or
+    None for history); the library allocates nothing (its scratch is a fixed
+    device array), see include/pdn.h."""
+    mat = Material()
+    for k in MATERIAL_KEYS:
+        setattr(mat, k, float(material[k]))
+    mat.seed = int(material["seed"])
+    ang = np.ascontiguousarray(ply_angle_deg, dtype=np.float64)
+    ptr = lambda t: None if t is None else C.c_void_p(t.data_ptr())
+    if stream is None:
+        stream = _current_stream()
+    rc = lib().pdn_internal_force_noalloc(int(n_nodes), int(n_hex), ptr(hex_dev), ptr(ply_dev), ptr(X_dev),
+                                          ptr(d_dev), ptr(history_dev), ptr(row_dev), ptr(col_dev), C.byref(mat),
+                                          _ptr(ang, C.c_double), len(ang), int(precision), int(damage_on),
+                                          int(plasticity_on), ptr(f_out_dev), stream)
+    if rc < 0:
+        raise PdnError(rc, (lib().pdn_last_error(None) or b"").decode())
 
 
 class Solver:

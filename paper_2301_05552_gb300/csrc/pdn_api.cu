@@ -919,3 +919,16 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
 }
 
 }  // extern "C"
+
+// Helpers for other translation units of the library (pdn_noalloc.cu).
+namespace pdn {
+void set_thread_error(const std::string &msg) { g_init_error = msg; }
+template <typename T>
+int fill_mat_public(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_plies, int damage_on,
+                    int plasticity_on, std::string &why) {
+  return fill_mat(M, m, ply_angle, n_plies, damage_on, plasticity_on, why);
+}
+template int fill_mat_public<float>(Mat<float> &, const pdn_material &, const double *, int, int, int, std::string &);
+template int fill_mat_public<double>(Mat<double> &, const pdn_material &, const double *, int, int, int,
+                                     std::string &);
+}  // namespace pdn
