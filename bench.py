@@ -220,7 +220,7 @@ def run_gpu(args, ws, rank, local):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    kernels_per_pass = 5 if plate.n_coh > 0 else 4
+    kernels_per_pass = 5 if plate.n_coh > 0 else 4  # contact, hex, coh, gather, tail
     gpu_launches = (K + repeats) * kernels_per_pass + 1  # + the target/mode kernel of the call
     value = ws * plate.n_hex * K / (ms * 1e-3)
 
@@ -280,6 +280,7 @@ def run_gpu(args, ws, rank, local):
                      "frac": achieved / peak_gbs, "traffic": traffic, "kernel": "k_hex<float>",
                      "alg_bytes_per_launch": alg, "launch_ms": hex_ms, "peak_kind": peak_kind},
         "kernel_ms": {k: v[0] for k, v in prof.items()},
+        "autotune": {"hex_variant": info["hex_variant"], "hex_ms_per_variant": info["tune_ms"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                 "seconds": t_e2e},
         "gpu_launches": gpu_launches,

@@ -159,6 +159,10 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int32_t status;          /* sticky device status (PDN_OK or an error code) */
   int32_t precision;
+  int32_t hex_variant;     /* hex-kernel launch variant chosen by the autotuner
+                              (occupancy target 4, 5, 6 or 3 blocks/SM for 0..3) */
+  int32_t reserved;
+  double tune_ms[4];       /* mean hex-kernel time of each variant when tuned (0 if not) */
 } pdn_info;
 
 /* Create a context on the current CUDA device: validate and copy the mesh,
@@ -255,7 +259,7 @@ void pdn_destroy(pdn_ctx *ctx);
  * quantity as pdn_internal_force, with the same element and gather kernels,
  * from caller buffers, and calls no allocating routine: its working memory
  * (element forces, mirrors, trial history, partial sums, control block,
- * about 10.5 MB) is a fixed array in device global memory that every device
+ * about 10.8 MB) is a fixed array in device global memory that every device
  * loading this library holds until the process exits.
  *
  * Device pointers (all caller-owned): hex [n_hex][8] and ply_of_hex [n_hex]

@@ -73,7 +73,8 @@ class Info(C.Structure):
     _fields_ = [("dt", C.c_double), ("dt_bulk", C.c_double), ("dt_coh", C.c_double), ("time", C.c_double),
                 ("f_peak", C.c_double), ("step", C.c_int64), ("n_active", C.c_int64), ("n_repeats", C.c_int64),
                 ("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
-                ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32)]
+                ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32),
+                ("hex_variant", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double * 4)]
 
 
 _lock = threading.Lock()
@@ -281,7 +282,9 @@ def pdn_internal_force(ctx: Context):
 def pdn_get_info(ctx: Context) -> dict:
     info = Info()
     _check(ctx, lib().pdn_get_info(ctx.handle, C.byref(info)))
-    return {k: getattr(info, k) for k, _ in Info._fields_}
+    out = {k: getattr(info, k) for k, _ in Info._fields_}
+    out["tune_ms"] = list(info.tune_ms)
+    return out
 
 
 def pdn_profile_kernels(ctx: Context, nsteps: int):

@@ -93,7 +93,13 @@ struct pdn_ctx {
   int max_repeats = 8;
   int64_t hist_cap = 0;
   bool has_imp = false;
+  bool tuned = false;
+  float tune_ms[4] = {0, 0, 0, 0};  // mean hex time per variant (autotuner)
   cudaGraphExec_t graph = nullptr;
+  // side stream for the interface kernel, forked from and joined back into
+  // the main stream inside every pass
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<cudaEvent_t> prof_ev;
   std::string err;
 
@@ -123,8 +129,9 @@ int cuda_fail(pdn_ctx *c, cudaError_t e, const char *where) {
   } while (0)
 
 cudaError_t run_pass(pdn_ctx *ctx, cudaEvent_t *ev) {
-  if (ctx->precision == PDN_FP64) return launch_pass<double>(ctx->Dd, ctx->Md, ctx->stream, kGatherBlock, ev);
-  return launch_pass<float>(ctx->Df, ctx->Mf, ctx->stream, kGatherBlock, ev);
+  if (ctx->precision == PDN_FP64)
+    return launch_pass<double>(ctx->Dd, ctx->Md, ctx->stream, kGatherBlock, ev, ctx->side, ctx->fork, ctx->join);
+  return launch_pass<float>(ctx->Df, ctx->Mf, ctx->stream, kGatherBlock, ev, ctx->side, ctx->fork, ctx->join);
 }
 
 cudaError_t build_graph(pdn_ctx *ctx) {
@@ -232,6 +239,15 @@ int fill_mat(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_pl
   M.g = (T)(m.GYT / m.GSL);
   M.Sp = (T)m.Sp;
   M.Kp = (T)m.Kp;
+  M.g1 = (T)(1.0 - m.GYT / m.GSL);
+  M.iXC = (T)(1.0 / m.XC);
+  {
+    const double ST = m.YC * ca * (sa + ca / t2);
+    M.iST2 = (T)(1.0 / (ST * ST));
+  }
+  M.kT = (T)(ca * (sa + ca / t2));  // ca (sa - etaT ca) with etaT = -1/tan(2 a0)
+  M.KpG12 = (T)(m.Kp * m.G12);
+  M.iG1Kp = (T)(1.0 / (m.G12 * (1.0 + m.Kp)));
   const double KI = m.KI;
   const double Ksh = KI * (m.GIc / m.GIIc) * (m.tauII / m.tauI) * (m.tauII / m.tauI);
   const double D3o = m.tauI / KI, D3c = 2.0 * m.GIc / m.tauI;
@@ -294,6 +310,9 @@ void pdn_destroy(pdn_ctx *ctx) {
   if (ctx->arena.base) cudaFree(ctx->arena.base);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
   delete ctx;
 }
 
@@ -331,6 +350,11 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     if (surf_of[j] >= 0) return bad("duplicate surface node id");
     surf_of[j] = (int32_t)s;
   }
+  for (int64_t c = 0; c < nc; ++c)
+    for (int a = 0; a < 4; ++a)
+      for (int i = 0; i < 3; ++i)
+        if (mesh->X[i * nn + mesh->coh[c * 8 + a]] != mesh->X[i * nn + mesh->coh[c * 8 + a + 4]])
+          return bad("interface element faces must coincide in the reference configuration (zero thickness)");
   if (mesh->fixed)
     for (int64_t j = 0; j < nn; ++j)
       if (mesh->fixed[j] > 7) return bad("fixed entries must be constraint bits 0..7");
@@ -396,6 +420,24 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
           return die(PDN_E_UNSTABLE, "element too large for the crack-band softening law (2 E G <= lc X^2)");
     }
   }
+  // Axis-aligned boxes whose corner coordinates coincide exactly in pairs in
+  // the element precision: then the higher trilinear modes of X vanish
+  // exactly in the kernel's butterfly and J is constant over the element.
+  bool all_boxes = true;
+  {
+    auto is_box = [&](int64_t e, auto tag) {
+      using T = decltype(tag);
+      const int32_t *c = mesh->hex + e * 8;
+      auto P = [&](int a, int i) { return (T)mesh->X[i * nn + c[a]]; };
+      return P(0, 0) == P(3, 0) && P(0, 0) == P(4, 0) && P(0, 0) == P(7, 0) && P(1, 0) == P(2, 0) &&
+             P(1, 0) == P(5, 0) && P(1, 0) == P(6, 0) && P(0, 1) == P(1, 1) && P(0, 1) == P(4, 1) &&
+             P(0, 1) == P(5, 1) && P(2, 1) == P(3, 1) && P(2, 1) == P(6, 1) && P(2, 1) == P(7, 1) &&
+             P(0, 2) == P(1, 2) && P(0, 2) == P(2, 2) && P(0, 2) == P(3, 2) && P(4, 2) == P(5, 2) &&
+             P(4, 2) == P(6, 2) && P(4, 2) == P(7, 2);
+    };
+    for (int64_t e = 0; e < nh && all_boxes; ++e)
+      all_boxes = opt->precision == PDN_FP64 ? is_box(e, double{}) : is_box(e, float{});
+  }
   // node -> element-force slot CSR (hexes ascending, then interfaces ascending)
   std::vector<int32_t> row(nn + 1, 0), col((size_t)(nh + nc) * 8);
   for (int64_t k = 0; k < nh * 8; ++k) row[mesh->hex[k] + 1]++;
@@ -408,6 +450,10 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     for (int64_t c = 0; c < nc; ++c)
       for (int a = 0; a < 8; ++a) col[fill[mesh->coh[c * 8 + a]]++] = (int32_t)((nh + c) * 8 + a);
   }
+  // inverse map: CSR position of every element slot (the element kernels
+  // write their nodal forces there)
+  std::vector<int32_t> pos(col.size());
+  for (size_t r = 0; r < col.size(); ++r) pos[col[r]] = (int32_t)r;
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
   double dtc = INFINITY;
@@ -456,10 +502,10 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   const size_t ts = fp64 ? 8 : 4;
   const int n_part = grid_of(nn, kGatherBlock);
   struct Ptrs {
-    int32_t *hex, *coh, *surf, *surf_of, *row, *col;
+    int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
-    uint8_t *nflag, *act[2], *rel;
+    uint8_t *nflag, *act[2], *rel, *pflag[2], *cflag[2];
     double *Xs, *mass, *d[2], *v[2], *nrm, *lam, *trial, *fhist, *fout;
     Partial *part;
     Ctl *ctl;
@@ -481,6 +527,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     P.Xs = A.take<double>(sizeof(double) * 3 * ns1);
     P.row = A.take<int32_t>(sizeof(int32_t) * (nn + 1));
     P.col = A.take<int32_t>(sizeof(int32_t) * (nh + nc) * 8);
+    P.pos = A.take<int32_t>(sizeof(int32_t) * (nh + nc) * 8);
     P.mass = A.take<double>(sizeof(double) * nn);
     P.imass = A.take<char>(ts * nn);
     for (int b = 0; b < 2; ++b) {
@@ -490,6 +537,8 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       P.hist[b] = A.take<char>(ts * 7 * 8 * nh);
       P.rD[b] = A.take<char>(ts * 4 * nc1);
       P.act[b] = A.take<uint8_t>(ns1);
+      P.pflag[b] = A.take<uint8_t>(nh);
+      P.cflag[b] = A.take<uint8_t>(nc1);
     }
     P.fe = A.take<char>(ts * 4 * (nh + nc) * 8);
     P.rel = A.take<uint8_t>(ns1);
@@ -537,6 +586,10 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("stream create: ") + cudaGetErrorString(ce));
     ctx->own_stream = true;
   }
+  ce = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming);
+  if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("side stream/events: ") + cudaGetErrorString(ce));
   ce = cudaMallocHost(&ctx->ctl_host, sizeof(Ctl));
   if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("pinned allocation: ") + cudaGetErrorString(ce));
 
@@ -584,6 +637,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   chk(up(d_Xs, Xs.data(), sizeof(double) * Xs.size()));
   chk(up(d_row, row.data(), sizeof(int32_t) * (nn + 1)));
   chk(up(d_col, col.data(), sizeof(int32_t) * col.size()));
+  chk(up(P.pos, pos.data(), sizeof(int32_t) * pos.size()));
   chk(up(d_mass, mass.data(), sizeof(double) * nn));
   chk(up(d_imass, imass.data(), imass.size()));
   for (int b = 0; b < 2; ++b) {
@@ -592,6 +646,8 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     chk(cudaMemset(d_u4[b], 0, ts * 4 * nn));
     chk(cudaMemset(d_rD[b], 0, ts * 4 * std::max<int64_t>(nc, 1)));
     chk(cudaMemset(d_act[b], 0, std::max<int64_t>(ns, 1)));
+    chk(cudaMemset(P.pflag[b], 1, nh));  // every element starts with the initial history
+    chk(cudaMemset(P.cflag[b], 1, std::max<int64_t>(nc, 1)));
     if (fp64)
       k_fill_hist_double<<<grid_of(nh * 8 * 7, 256), 256>>>(reinterpret_cast<double *>(d_hist[b]), nh * 8, 4);
     else
@@ -638,6 +694,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     D.Xs = d_Xs;
     D.row = d_row;
     D.col = d_col;
+    D.pos = P.pos;
     D.mass = d_mass;
     D.inv_mass = reinterpret_cast<const T *>(d_imass);
     for (int b = 0; b < 2; ++b) {
@@ -647,6 +704,8 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       D.hist[b] = reinterpret_cast<T *>(d_hist[b]);
       D.rD[b] = reinterpret_cast<T *>(d_rD[b]);
       D.act[b] = d_act[b];
+      D.pflag[b] = P.pflag[b];
+      D.cflag[b] = P.cflag[b];
     }
     D.fe = reinterpret_cast<V4 *>(d_fe);
     D.rel = d_rel;
@@ -663,7 +722,11 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     D.fout = d_fout;
     D.dt = ctx->dt;
     D.phi = ctx->phi;
-    for (int i = 0; i < 3; ++i) D.grav[i] = ctx->grav[i];
+    for (int i = 0; i < 3; ++i) {
+      D.grav[i] = ctx->grav[i];
+      D.grav_t[i] = (T)ctx->grav[i];
+    }
+    D.all_boxes = all_boxes ? 1 : 0;
   };
   if (fp64)
     wire(ctx->Dd, double{});
@@ -689,8 +752,49 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
   s.M = mass;
   s.has = 1;
   PDN_CU(cudaMemcpyAsync(ctx->imp_dev, &s, sizeof(Striker), cudaMemcpyHostToDevice, ctx->stream), "set impactor");
+  StrikerStep *ss = ctx->precision == PDN_FP64 ? ctx->Dd.imp_step : ctx->Df.imp_step;
+  PDN_CU(launch_striker_init(ctx->imp_dev, ss, ctx->dt, ctx->stream), "striker init");
   PDN_CU(cudaStreamSynchronize(ctx->stream), "set impactor");
   ctx->has_imp = true;
+  return PDN_OK;
+}
+
+// Autotuner: times every hex-kernel variant on force-evaluation passes of the
+// committed state (no side effect on the simulation) and keeps the fastest.
+// The variants differ only in their register budget, not in arithmetic, so
+// the choice never changes a result.  Runs once per context, before the step
+// graph is captured.
+int autotune(pdn_ctx *ctx) {
+  if (ctx->tuned) return PDN_OK;
+  ctx->tuned = true;
+  const int nvar = ctx->precision == PDN_FP64 ? 1 : 4;
+  if (nvar == 1) return PDN_OK;
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; ++k) PDN_CU(cudaEventCreate(&ev[k]), "tune event");
+  int best = 0;
+  float best_ms = 1e30f;
+  const int reps = 3;
+  for (int v = 0; v < nvar; ++v) {
+    ctx->Df.hex_variant = v;
+    float sum = 0.f;
+    for (int r = 0; r <= reps; ++r) {
+      int rc = set_mode(ctx, MODE_FORCES, ctx->ctl_host->step);
+      if (rc) return rc;
+      cudaError_t e = run_pass(ctx, ev);  // ev[1] .. ev[2] bracket the hex kernel
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune pass");
+      PDN_CU(cudaStreamSynchronize(ctx->stream), "autotune");
+      float ms = 0.f;
+      PDN_CU(cudaEventElapsedTime(&ms, ev[1], ev[2]), "autotune time");
+      if (r > 0) sum += ms;  // the first pass warms up
+    }
+    ctx->tune_ms[v] = sum / reps;
+    if (ctx->tune_ms[v] < best_ms) {
+      best_ms = ctx->tune_ms[v];
+      best = v;
+    }
+  }
+  ctx->Df.hex_variant = best;
+  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
   return PDN_OK;
 }
 
@@ -702,6 +806,8 @@ int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
   if (rc) return rc;
   if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "device halted earlier (sticky status)");
   if (nsteps == 0) return PDN_OK;
+  rc = autotune(ctx);
+  if (rc) return rc;
   const int64_t target = ctx->ctl_host->step + nsteps;
   rc = set_mode(ctx, MODE_ADVANCE, target);
   if (rc) return rc;
@@ -915,6 +1021,9 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
   info->device_bytes = (int64_t)ctx->arena.size;
   info->status = c.status;
   info->precision = ctx->precision;
+  info->hex_variant = ctx->precision == PDN_FP64 ? ctx->Dd.hex_variant : ctx->Df.hex_variant;
+  info->reserved = 0;
+  for (int v = 0; v < 4; ++v) info->tune_ms[v] = ctx->tune_ms[v];
   return PDN_OK;
 }
 

@@ -75,6 +75,8 @@ struct Mat {
   T ca, sa, etaT, ST, etaLc;  // fracture-plane constants; etaL = SL * etaLc
   T g;                        // GYT / GSL
   T Sp, Kp;
+  // derived: 1 - g, 1/XC, 1/ST^2, ca (sa - etaT ca), Kp G12, 1/(G12 (1 + Kp))
+  T g1, iXC, iST2, kT, KpG12, iG1Kp;
   // interface
   T KI, Ksh, KI_D3o2, Ksh_Dsho2, KI_D3oD3c, Ksh_DshoDshc, eta, onset_floor;
   T spread;
@@ -110,6 +112,7 @@ struct Dev {
   const double *Xs;        // [3][ns] surface reference coordinates (FP64)
   const int32_t *row;      // [nn + 1] CSR of node -> element-force slot
   const int32_t *col;      // [nnz] slot = 8*e + k (hex), 8*(nh + c) + k (interface)
+  const int32_t *pos;      // [nnz] inverse of col: CSR position of slot (e, k)
   const double *mass;      // [nn]
   const T *inv_mass;       // [nn]
   // state (double buffered)
@@ -117,6 +120,12 @@ struct Dev {
   V4 *u4[2];               // [nn] element-precision mirror of d
   T *hist[2];              // [7][8][nh] history per Gauss point
   T *rD[2];                // [4][nc] interface thresholds
+  // 1 = every point of the element still holds the initial history (r = 1,
+  // plastic strain 0; interface r_D = 0): its history is neither read nor
+  // written.  Double-buffered with the history; nullptr = no flags (history
+  // always read and written).
+  uint8_t *pflag[2];       // [nh]
+  uint8_t *cflag[2];       // [nc]
   V4 *fe;                  // [(nh + nc) * 8] element nodal forces
   // contact
   uint8_t *act[2];         // [ns] contact set by step parity
@@ -136,12 +145,22 @@ struct Dev {
   // integration
   double dt, phi;
   double grav[3];
+  T grav_t[3];  // gravity in the element precision
+  // every hex is an axis-aligned box whose corner coordinates coincide
+  // exactly in pairs (in T): the trilinear map is affine and J is constant
+  int32_t all_boxes;
+  // launch configuration picked by the autotuner: hex occupancy variant
+  // (0: 4 blocks of 128 per SM, 1: 5, 2: 6, 3: 3).  The variants execute the
+  // same arithmetic, so the choice does not change any result.
+  int32_t hex_variant;
 };
 
 // Launchers (pdn_kernels.cu).
 template <typename T>
 cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_t gather_block,
-                        cudaEvent_t *ev /* [2 * 5] or nullptr */);
+                        cudaEvent_t *ev /* [6] or nullptr */, cudaStream_t side = nullptr,
+                        cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
+cudaError_t launch_striker_init(Striker *S, StrikerStep *ss, double dt, cudaStream_t s);
 template <typename T>
 cudaError_t launch_damage_field(const Dev<T> &D, const Mat<T> &M, int which, float *out,
                                 cudaStream_t s);

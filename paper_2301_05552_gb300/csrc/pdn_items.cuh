@@ -1,0 +1,719 @@
+// Per-item bodies of the step kernels (one contact-surface node, one hex8,
+// one interface element, one block of nodes for the gather, the tail of a
+// pass), shared by the per-pass kernels (pdn_kernels.cu) and the batched
+// persistent kernel (pdn_batch.cu).
+#pragma once
+
+#include <cstdint>
+
+#include "pdn.h"
+#include "pdn_device.cuh"
+#include "pdn_internal.h"
+
+namespace pdn {
+namespace detail {
+
+// ---------------------------------------------------------------------------
+// Kernel 1: contact detection and projection (Sec. 2.1, Fig. 1, Algorithm 1).
+// One thread per contact-surface node.  The striker state of the step being
+// computed (its RK4 update with the committed contact force held over the
+// step, Eq. rk4) was produced by the tail of the previous pass, or by
+// k_striker_init after pdn_set_impactor; this kernel only reads it.
+template <typename T>
+__device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  const Ctl *ctl = D.ctl;
+  if (s >= D.ns) return;
+  const Striker *S = D.imp;
+  const StrikerStep *ss = D.imp_step;
+  const int64_t nn = D.nn, ns = D.ns;
+  const int64_t j = D.surf[s];
+  const int cur = ctl->dpar;
+  const int spar = (int)((ctl->step + 1) & 1), ppar = (int)(ctl->step & 1);
+  double *d = D.d[cur];
+  double *v = D.v[cur];
+  if (mode == MODE_ADVANCE) {
+    D.rel[s] = 0;
+    uint8_t a = 0;
+    const uint8_t fl = D.nflag[j];
+    const bool was_active = D.act[ppar][s] != 0;
+    bool near = was_active;
+    if (!near && S->has && (fl & 7) != 7) {
+      // FP32 prefilter: nodes farther than R + 0.05 mm from the centre cannot
+      // be in contact (the FP32 distance error here is below 1e-4 mm); only
+      // the others take the FP64 gap test below.
+      const V4 xr = D.X4[j];
+      const V4 ur = D.u4[cur][j];
+      const float dx = (float)xr.x + (float)ur.x - (float)ss->c[0];
+      const float dy = (float)xr.y + (float)ur.y - (float)ss->c[1];
+      const float dz = (float)xr.z + (float)ur.z - (float)ss->c[2];
+      const float mag = fabsf((float)xr.x) + fabsf((float)xr.y) + fabsf((float)xr.z);
+      const float rr = (float)S->R + 0.05f + 4e-6f * mag;
+      near = dx * dx + dy * dy + dz * dz < rr * rr;
+    }
+    if (near && S->has && (fl & 7) != 7) {
+      double x[3], r2 = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        x[i] = D.Xs[i * ns + s] + d[i * nn + j] - ss->c[i];
+        r2 += x[i] * x[i];
+      }
+      const double r = sqrt(r2);
+      const double gap = r - S->R;
+      if (gap < 0.0 || was_active) {
+        a = 1;
+        const double ir = 1.0 / r;
+        double n[3] = {x[0] * ir, x[1] * ir, x[2] * ir};
+        double dj[3], vj[3], vn = 0.0, wn = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dj[i] = d[i * nn + j];
+          vj[i] = v[i * nn + j];
+          D.trial[i * ns + s] = dj[i];
+          D.trial[(3 + i) * ns + s] = vj[i];
+          vn += vj[i] * n[i];
+          wn += ss->w[i] * n[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          if (!((fl >> i) & 1)) {
+            dj[i] -= gap * n[i];
+            vj[i] += (wn - vn) * n[i];
+          }
+          d[i * nn + j] = dj[i];
+          v[i * nn + j] = vj[i];
+          D.nrm[i * ns + s] = n[i];
+        }
+        V4 u;
+        u.x = (T)dj[0];
+        u.y = (T)dj[1];
+        u.z = (T)dj[2];
+        u.w = T(0);
+        D.u4[cur][j] = u;
+      }
+    }
+    D.act[spar][s] = a;
+  } else {  // MODE_REPEAT: restore the released nodes to their trial state
+    if (D.rel[s] && D.act[spar][s]) {
+      double dj[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        dj[i] = D.trial[i * ns + s];
+        d[i * nn + j] = dj[i];
+        v[i * nn + j] = D.trial[(3 + i) * ns + s];
+      }
+      V4 u;
+      u.x = (T)dj[0];
+      u.y = (T)dj[1];
+      u.z = (T)dj[2];
+      u.w = T(0);
+      D.u4[cur][j] = u;
+      D.act[spar][s] = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 2: hex8 internal forces, total Lagrangian, 2x2x2 Gauss (Sec. 2,
+// Eq. fcont), with the intralaminar law per Gauss point.  One thread per
+// element; geometry and displacement enter through their trilinear modes, so
+// that J = [dx/dxi], du/dxi and the returned force are cheap mode sums.
+// f_a = sum_g sum_k dN_a/dxi_k Q_g[k][:],  Q_g = det J_g  J_g^-1 P_g,
+// P = S F^T (nominal stress), S rotated from ply axes (angle about z).
+// BOX: every element is an axis-aligned box (checked on the host), so J is
+// the constant diagonal diag((x6-x0)/2, (y6-y0)/2, (z6-z0)/2).
+// The next Gauss point's history is loaded while the current one computes.
+template <typename T, bool BOX>
+__device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64_t e, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  const Ctl *ctl = D.ctl;
+  if (e >= D.nh) return;
+  const int64_t nh = D.nh;
+  const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+  const int hb = ctl->hpar;
+  const V4 *__restrict__ U = D.u4[ub];
+  const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
+  const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
+  const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const T *__restrict__ hin = D.hist[hb] + e;
+  T *__restrict__ hout = D.hist[hb ^ 1] + e;
+  // An element whose points all still hold the initial history skips the
+  // history traffic: it is not read, and written only once a point changes.
+  const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][e] != 0;
+  bool dirty = false;
+  // history of Gauss point 0 in flight first
+  T hn[7];
+#pragma unroll
+  for (int f = 0; f < 7; ++f) hn[f] = pristine_in ? (f < 4 ? T(1) : T(0)) : hin[(int64_t)(f * 8) * nh];
+  T am[8][3], bm[8][3];
+  T jd[3] = {T(0), T(0), T(0)}, wd[3] = {T(0), T(0), T(0)}, vol = T(0);
+  {
+    T ua[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const V4 u = U[nd[a]];
+      ua[a][0] = u.x;
+      ua[a][1] = u.y;
+      ua[a][2] = u.z;
+    }
+    to_modes(ua, bm);
+    if constexpr (BOX) {
+      const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
+      const T J0 = T(0.5) * (x6.x - x0.x), J1 = T(0.5) * (x6.y - x0.y), J2 = T(0.5) * (x6.z - x0.z);
+      const T det = J0 * (J1 * J2);
+      jd[0] = T(1) / J0;
+      jd[1] = T(1) / J1;
+      jd[2] = T(1) / J2;
+      wd[0] = det * jd[0];
+      wd[1] = det * jd[1];
+      wd[2] = det * jd[2];
+      vol = T(8) * det;
+    } else {
+      T xa[8][3];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const V4 x = D.X4[nd[a]];
+        xa[a][0] = x.x;
+        xa[a][1] = x.y;
+        xa[a][2] = x.z;
+      }
+      to_modes(xa, am);
+    }
+  }
+  const int ply = D.ply[e];
+  const T cs = M.ply_c[ply], sn = M.ply_s[ply];
+  const T c2 = cs * cs, s2 = sn * sn, csn = cs * sn;
+  const ElemLaw<T> L = elem_law(M, e);
+  T lc = T(-1);
+  T C[8][3];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) C[m][0] = C[m][1] = C[m][2] = T(0);
+  const T gp = T(0.57735026918962576451);
+#pragma unroll 1
+  for (int g = 0; g < 8; ++g) {
+    T h[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) h[f] = hn[f];
+    if (g < 7 && !pristine_in) {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) hn[f] = hin[(int64_t)(f * 8 + g + 1) * nh];
+    }
+    const T xi = T(sgn_x(g)) * gp, et = T(sgn_y(g)) * gp, ze = T(sgn_z(g)) * gp;
+    T Du[3][3], H[3][3], Ji[3][3], det = T(0);
+    jac_cols(bm, xi, et, ze, Du);
+    if constexpr (BOX) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) H[i][k] = Du[i][k] * jd[k];
+    } else {
+      T J[3][3];
+      jac_cols(am, xi, et, ze, J);
+      det = det3(J);
+      const T id = T(1) / det;
+      Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * id;
+      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+      Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * id;
+      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+      Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * id;
+      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) H[i][k] = Du[i][0] * Ji[0][k] + Du[i][1] * Ji[1][k] + Du[i][2] * Ji[2][k];
+    }
+    // Green strain E = 1/2 (H + H^T + H^T H)
+    T E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = i; k < 3; ++k) {
+        E[i][k] = T(0.5) * (H[i][k] + H[k][i] + H[0][i] * H[0][k] + H[1][i] * H[1][k] + H[2][i] * H[2][k]);
+        E[k][i] = E[i][k];
+      }
+    // to ply axes (rotation about z): Em = R^T E R
+    T ep[6];
+    ep[0] = c2 * E[0][0] + T(2) * csn * E[0][1] + s2 * E[1][1];
+    ep[1] = s2 * E[0][0] - T(2) * csn * E[0][1] + c2 * E[1][1];
+    ep[2] = E[2][2];
+    ep[3] = T(2) * (-csn * E[0][0] + (c2 - s2) * E[0][1] + csn * E[1][1]);
+    ep[4] = T(2) * (cs * E[0][2] + sn * E[1][2]);
+    ep[5] = T(2) * (-sn * E[0][2] + cs * E[1][2]);
+    T sm[6];
+    if constexpr (BOX)
+      cdm(M, L, (const T(*)[3]) nullptr, vol, lc, ep, h, sm);
+    else
+      cdm(M, L, (const T(*)[3])am, T(0), lc, ep, h, sm);
+    if (!pristine_in) {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + g) * nh] = h[f];
+    } else {
+      const bool changed = h[0] > T(1) || h[1] > T(1) || h[2] > T(1) || h[3] > T(1) || h[4] != T(0) ||
+                           h[5] != T(0) || h[6] != T(0);
+      if (changed && !dirty) {
+        // first change in a pristine element: the earlier points keep the
+        // initial history, which the output buffer does not hold yet
+        for (int gg = 0; gg < g; ++gg)
+#pragma unroll
+          for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + gg) * nh] = f < 4 ? T(1) : T(0);
+        dirty = true;
+      }
+      if (dirty) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + g) * nh] = h[f];
+      }
+    }
+    // back to global axes: S = R Sm R^T
+    T S[3][3];
+    S[0][0] = c2 * sm[0] - T(2) * csn * sm[3] + s2 * sm[1];
+    S[1][1] = s2 * sm[0] + T(2) * csn * sm[3] + c2 * sm[1];
+    S[2][2] = sm[2];
+    S[0][1] = S[1][0] = csn * sm[0] + (c2 - s2) * sm[3] - csn * sm[1];
+    S[0][2] = S[2][0] = cs * sm[4] - sn * sm[5];
+    S[1][2] = S[2][1] = sn * sm[4] + cs * sm[5];
+    // P = S F^T with F = I + H; Q = det J^-1 P
+    T P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        P[i][k] = S[i][k] + S[i][0] * H[k][0] + S[i][1] * H[k][1] + S[i][2] * H[k][2];
+    T Q[3][3];
+    if constexpr (BOX) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int I = 0; I < 3; ++I) Q[k][I] = wd[k] * P[k][I];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int I = 0; I < 3; ++I) Q[k][I] = det * (Ji[k][0] * P[0][I] + Ji[k][1] * P[1][I] + Ji[k][2] * P[2][I]);
+    }
+#pragma unroll
+    for (int I = 0; I < 3; ++I) {
+      C[1][I] += Q[0][I];
+      C[2][I] += Q[1][I];
+      C[3][I] += Q[2][I];
+      C[4][I] += et * Q[0][I] + xi * Q[1][I];
+      C[5][I] += ze * Q[1][I] + et * Q[2][I];
+      C[6][I] += ze * Q[0][I] + xi * Q[2][I];
+      C[7][I] += et * ze * Q[0][I] + xi * ze * Q[1][I] + xi * et * Q[2][I];
+    }
+  }
+  if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
+  T f[8][3];
+  from_modes(C, f);
+  // element forces go straight to their CSR positions, so that the gather
+  // reads each node's contributions as one contiguous run
+  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e);
+  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e + 1);
+  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    V4 o;
+    o.x = f[a][0];
+    o.y = f[a][1];
+    o.z = f[a][2];
+    o.w = T(0);
+    D.fe[ps[a]] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 3: zero-thickness interface elements with Newton-Cotes integration
+// (Sec. 2.3.2) and the cohesive law (Algorithm 5).  One thread per element.
+template <typename T>
+__device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64_t c, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  const Ctl *ctl = D.ctl;
+  if (c >= D.nc) return;
+  const int64_t nc = D.nc;
+  const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+  const int hb = ctl->hpar;
+  const V4 *__restrict__ U = D.u4[ub];
+  const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
+  const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
+  const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  constexpr int QX[4] = {-1, 1, 1, -1}, QY[4] = {-1, -1, 1, 1};
+  // the upper face coincides with the lower one in the reference
+  // configuration (zero thickness), so the lower face gives the mid-surface
+  T xm[4][3], uu[8][3];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const V4 xb = D.X4[nd[a]];
+    xm[a][0] = xb.x;
+    xm[a][1] = xb.y;
+    xm[a][2] = xb.z;
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const V4 u = U[nd[a]];
+    uu[a][0] = u.x;
+    uu[a][1] = u.y;
+    uu[a][2] = u.z;
+  }
+  // frame at the element centre
+  T e1[3], e2[3], e3[3];
+  {
+    T tx[3] = {T(0), T(0), T(0)}, ty[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        tx[i] += T(0.25) * T(QX[a]) * xm[a][i];
+        ty[i] += T(0.25) * T(QY[a]) * xm[a][i];
+      }
+    const T n0 = tx[1] * ty[2] - tx[2] * ty[1], n1 = tx[2] * ty[0] - tx[0] * ty[2],
+            n2 = tx[0] * ty[1] - tx[1] * ty[0];
+    const T inn = T(1) / xsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const T itn = T(1) / xsqrt(tx[0] * tx[0] + tx[1] * tx[1] + tx[2] * tx[2]);
+    e3[0] = n0 * inn;
+    e3[1] = n1 * inn;
+    e3[2] = n2 * inn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e1[i] = tx[i] * itn;
+    e2[0] = e3[1] * e1[2] - e3[2] * e1[1];
+    e2[1] = e3[2] * e1[0] - e3[0] * e1[2];
+    e2[2] = e3[0] * e1[1] - e3[1] * e1[0];
+  }
+  const T *__restrict__ rin = D.rD[hb];
+  T *__restrict__ rout = D.rD[hb ^ 1];
+  // undamaged interface elements (all r_D = 0) skip the threshold traffic
+  const bool pristine_in = D.cflag[0] != nullptr && D.cflag[hb][c] != 0;
+  T rv[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) rv[p] = pristine_in ? T(0) : rin[(int64_t)p * nc + c];
+  T f[8][3];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const T xi = T(QX[p]), et = T(QY[p]);
+    T tx[3] = {T(0), T(0), T(0)}, ty[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const T dxi = T(0.25) * T(QX[a]) * (T(1) + et * T(QY[a]));
+      const T deta = T(0.25) * T(QY[a]) * (T(1) + xi * T(QX[a]));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        tx[i] += dxi * xm[a][i];
+        ty[i] += deta * xm[a][i];
+      }
+    }
+    const T n0 = tx[1] * ty[2] - tx[2] * ty[1], n1 = tx[2] * ty[0] - tx[0] * ty[2],
+            n2 = tx[0] * ty[1] - tx[1] * ty[0];
+    const T w = xsqrt(n0 * n0 + n1 * n1 + n2 * n2);
+    const T dg0 = uu[p + 4][0] - uu[p][0], dg1 = uu[p + 4][1] - uu[p][1], dg2 = uu[p + 4][2] - uu[p][2];
+    const T dl[3] = {e1[0] * dg0 + e1[1] * dg1 + e1[2] * dg2, e2[0] * dg0 + e2[1] * dg1 + e2[2] * dg2,
+                     e3[0] * dg0 + e3[1] * dg1 + e3[2] * dg2};
+    T tau[3], r1;
+    czm(M, dl, rv[p], r1, tau);
+    rv[p] = r1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const T tg = w * (tau[0] * e1[i] + tau[1] * e2[i] + tau[2] * e3[i]);
+      f[p + 4][i] = tg;
+      f[p][i] = -tg;
+    }
+  }
+  const bool still = pristine_in && rv[0] == T(0) && rv[1] == T(0) && rv[2] == T(0) && rv[3] == T(0);
+  if (!still) {
+#pragma unroll
+    for (int p = 0; p < 4; ++p) rout[(int64_t)p * nc + c] = rv[p];
+  }
+  if (D.cflag[0] != nullptr) D.cflag[hb ^ 1][c] = still ? 1 : 0;
+  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c));
+  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c) + 1);
+  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    V4 o;
+    o.x = f[a][0];
+    o.y = f[a][1];
+    o.z = f[a][2];
+    o.w = T(0);
+    D.fe[ps[a]] = o;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Tail of a pass (one block, after the gather).  Sums the gather
+// partials in a fixed order, then commits the step (contact force
+// F = sum lambda_j n_j to the striker, Sec. 2.2.2; step counter, history and
+// node-buffer parities, force history), or marks the step for repetition when
+// adhesive nodes were released (Algorithm 2: the MPI_MAX of kfl_reset becomes
+// this single-block decision), or halts.  On commit it also advances the
+// striker for the next pass (RK4 with the committed force).
+template <typename T>
+__device__ void tail_block(const Dev<T> &D, int mode) {
+  Ctl *ctl = D.ctl;
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  int nact = 0, nadh = 0, nonfin = 0;
+  // Each thread sums its strided partials in index order.  Only blocks that
+  // held active contact nodes carry a non-zero force, and FP64 adds run at a
+  // small fraction of the integer rate on this part, so the doubles are
+  // touched only for those partials (the counts decide, in integer).
+#pragma unroll 4
+  for (int k = threadIdx.x; k < D.n_part; k += blockDim.x) {
+    const Partial &pk = D.part[k];
+    const int na = pk.n_act;
+    if (na > 0) {
+      f0 += pk.f[0];
+      f1 += pk.f[1];
+      f2 += pk.f[2];
+    }
+    nact += na;
+    nadh += pk.n_adh;
+    nonfin |= pk.nonfinite;
+  }
+  const bool warp_has_force = __any_sync(0xffffffffu, nact > 0);
+  if (warp_has_force) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nact += __shfl_xor_sync(0xffffffffu, nact, o);
+    nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
+    nonfin |= __shfl_xor_sync(0xffffffffu, nonfin, o);
+  }
+  __shared__ double tf[3][32];
+  __shared__ int ti[3][32];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    tf[0][w] = f0;
+    tf[1][w] = f1;
+    tf[2][w] = f2;
+    ti[0][w] = nact;
+    ti[1][w] = nadh;
+    ti[2][w] = nonfin;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  // The control block and the striker are read into registers once and
+  // written back once: through pointers every field access would be a
+  // separate dependent global round trip.
+  Ctl c = *ctl;
+  double F[3] = {0.0, 0.0, 0.0};
+  int na = 0, nd = 0, nf = 0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+    if (ti[0][k] > 0) {
+      F[0] += tf[0][k];
+      F[1] += tf[1][k];
+      F[2] += tf[2][k];
+    }
+    na += ti[0][k];
+    nd += ti[1][k];
+    nf |= ti[2][k];
+  }
+  if (mode == MODE_FORCES) {
+    c.mode = MODE_DONE;
+  } else if (nf) {
+    c.status = PDN_E_NONFINITE;
+    c.mode = MODE_HALT;
+  } else if (mode == MODE_PRIME) {
+    c.dpar ^= 1;
+    c.mode = (c.step >= c.target) ? MODE_DONE : MODE_ADVANCE;
+  } else if (nd > 0) {
+    if (c.repeats >= c.max_repeats) {
+      c.status = PDN_E_RELEASE_LIMIT;
+      c.mode = MODE_HALT;
+    } else {
+      c.repeats += 1;
+      c.n_repeats_total += 1;
+      c.mode = MODE_REPEAT;
+    }
+  } else {
+    // commit step n+1
+    Striker S = *D.imp;
+    const StrikerStep ss = *D.imp_step;
+    for (int i = 0; i < 3; ++i) {
+      S.c[i] = ss.c[i];
+      S.w[i] = ss.w[i];
+      S.F[i] = F[i];
+    }
+    const double fc = F[0] * S.axis[0] + F[1] * S.axis[1] + F[2] * S.axis[2];
+    if (c.hist_count < D.hist_cap) D.fhist[c.hist_count++] = fc;
+    if (fc > c.f_peak) c.f_peak = fc;
+    c.n_active = na;
+    c.step += 1;
+    c.time += D.dt;
+    c.dpar ^= 1;
+    c.hpar ^= 1;
+    c.repeats = 0;
+    c.mode = (c.step >= c.target) ? MODE_DONE : MODE_ADVANCE;
+    // striker of the next step (Algorithm 1: the rigid instance moves first,
+    // with the contact force just committed)
+    StrikerStep nx;
+    striker_rk4(S, D.dt, nx.c, nx.w, nx.aI);
+    *D.imp = S;
+    *D.imp_step = nx;
+  }
+  *ctl = c;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 4: deterministic CSR gather of element forces per node (fixed
+// ascending order: hexes, then interface elements), lumped-mass acceleration
+// a = m^-1 (f^e - f^i) (Sec. 2.2.1), contact reaction of active nodes
+// lambda = m (a_I . n) - f . n with release of adhesive nodes (Eq. anodes,
+// Algorithm 2), and the Tchamwa-Wielgosz predictor of the next step:
+// v' = v + dt a, d' = d + dt v + phi dt^2 a.  One thread per node; per-block
+// reaction partial sums in a fixed tree order.
+// Called by every thread of a block: node j0 + threadIdx.x, block partial
+// written to D.part[part_index].
+template <typename T>
+__device__ __forceinline__ void gather_items(const Dev<T> &D, int64_t j0, int64_t part_index, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  const Ctl *ctl = D.ctl;
+  const int64_t j = j0 + threadIdx.x;
+  const int64_t nn = D.nn;
+  double pf0 = 0.0, pf1 = 0.0, pf2 = 0.0;
+  int nact = 0, nadh = 0, nonfin = 0;
+  if (j < nn) {
+    T fx = T(0), fy = T(0), fz = T(0);
+    const int r0 = D.row[j], r1 = D.row[j + 1];
+    // the node's element forces are contiguous (written at their CSR
+    // positions); summed in CSR order: hexes, then interfaces, ascending
+#pragma unroll 4
+    for (int r = r0; r < r1; ++r) {
+      const V4 f = D.fe[r];
+      fx += f.x;
+      fy += f.y;
+      fz += f.z;
+    }
+    if (mode == MODE_FORCES) {
+      D.fout[j] = (double)fx;
+      D.fout[nn + j] = (double)fy;
+      D.fout[2 * nn + j] = (double)fz;
+    } else {
+      const int cur = ctl->dpar, nxt = cur ^ 1;
+      const uint8_t fl = D.nflag[j];
+      double a[3];
+      bool done = false;
+      if ((fl & 8) && mode != MODE_PRIME) {
+        const int64_t s = D.surf_of[j];
+        const int spar = (int)((ctl->step + 1) & 1);
+        if (D.act[spar][s]) {
+          const int64_t ns = D.ns;
+          const double m = D.mass[j];
+          const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
+          const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy,
+                                m * D.grav[2] - (double)fz};
+          const StrikerStep *ss = D.imp_step;
+          const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
+          const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
+          const double lam = m * adot - fdot;
+          D.lam[s] = lam;
+          if (lam < 0.0) {
+            D.rel[s] = 1;
+            nadh = 1;
+            a[0] = fr[0] / m;
+            a[1] = fr[1] / m;
+            a[2] = fr[2] / m;
+          } else {
+            nact = 1;
+            pf0 = lam * n[0];
+            pf1 = lam * n[1];
+            pf2 = lam * n[2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
+          }
+          done = true;
+        }
+      }
+      if (!done) {
+        // free node: acceleration in the element precision, checked before
+        // widening (the element force is already rounded to T)
+        const T im = D.inv_mass[j];
+        const T ax = D.grav_t[0] - fx * im, ay = D.grav_t[1] - fy * im, az = D.grav_t[2] - fz * im;
+        if (!xfinite(ax) || !xfinite(ay) || !xfinite(az)) nonfin = 1;
+        a[0] = to_f64(ax);
+        a[1] = to_f64(ay);
+        a[2] = to_f64(az);
+      } else if (!xfinite(a[0]) || !xfinite(a[1]) || !xfinite(a[2])) {
+        nonfin = 1;
+      }
+      const double dt = D.dt;
+      const double *dc = D.d[cur];
+      const double *vc = D.v[cur];
+      double *dn = D.d[nxt];
+      double *vn = D.v[nxt];
+      double dd[3];
+      const bool phi1 = (D.phi == 1.0);
+      const double pdt2 = D.phi * dt * dt;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
+        const double vi = vc[i * nn + j];
+        const double di = dc[i * nn + j];
+        const double v1 = vi + dt * ai;
+        const double d1 = phi1 ? di + dt * v1 : di + dt * vi + pdt2 * ai;
+        vn[i * nn + j] = v1;
+        dn[i * nn + j] = d1;
+        dd[i] = d1;
+      }
+      V4 u;
+      u.x = to_elem(dd[0], T(0));
+      u.y = to_elem(dd[1], T(0));
+      u.z = to_elem(dd[2], T(0));
+      u.w = T(0);
+      D.u4[nxt][j] = u;
+    }
+  }
+  // block partials (fixed order: warp butterfly, then warps in index order)
+  __shared__ double sf[3][8];
+  __shared__ int si[3][8];
+  const int any = __syncthreads_or(nact | nadh | nonfin);
+  if (any) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      pf0 += __shfl_xor_sync(0xffffffffu, pf0, o);
+      pf1 += __shfl_xor_sync(0xffffffffu, pf1, o);
+      pf2 += __shfl_xor_sync(0xffffffffu, pf2, o);
+      nact += __shfl_xor_sync(0xffffffffu, nact, o);
+      nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
+      nonfin |= __shfl_xor_sync(0xffffffffu, nonfin, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      sf[0][w] = pf0;
+      sf[1][w] = pf1;
+      sf[2][w] = pf2;
+      si[0][w] = nact;
+      si[1][w] = nadh;
+      si[2][w] = nonfin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Partial p;
+      p.f[0] = p.f[1] = p.f[2] = 0.0;
+      p.n_act = p.n_adh = p.nonfinite = p.pad = 0;
+      const int nw = blockDim.x >> 5;
+      for (int k = 0; k < nw; ++k) {
+        p.f[0] += sf[0][k];
+        p.f[1] += sf[1][k];
+        p.f[2] += sf[2][k];
+        p.n_act += si[0][k];
+        p.n_adh += si[1][k];
+        p.nonfinite |= si[2][k];
+      }
+      D.part[part_index] = p;
+    }
+  } else if (threadIdx.x == 0) {
+    Partial p;
+    p.f[0] = p.f[1] = p.f[2] = 0.0;
+    p.n_act = p.n_adh = p.nonfinite = p.pad = 0;
+    D.part[part_index] = p;
+  }
+}
+
+
+}  // namespace detail
+}  // namespace pdn

@@ -49,7 +49,9 @@ constexpr size_t kOffU4 = kOffX4 + round256(kNodeV4Bytes);
 constexpr size_t kOffHin = kOffU4 + round256(kNodeV4Bytes);
 constexpr size_t kOffHout = kOffHin + round256(kHistBytes);
 constexpr size_t kOffFe = kOffHout + round256(kHistBytes);
-constexpr size_t kScratchBytes = kOffFe + round256(kFeBytes);
+constexpr size_t kPosBytes = (size_t)PDN_NOALLOC_MAX_HEX * 8 * sizeof(int32_t);
+constexpr size_t kOffPos = kOffFe + round256(kFeBytes);
+constexpr size_t kScratchBytes = kOffPos + round256(kPosBytes);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -89,6 +91,15 @@ __global__ void k_noalloc_prepare(Ctl *ctl, const double *X, const double *d, ty
   }
 }
 
+// CSR position of every element slot: the inverse of the caller's csr_col
+// (the element kernel writes each nodal force at its node's CSR position).
+__global__ void k_noalloc_pos(const int32_t *col, int32_t *pos, int64_t nnz) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nnz) return;
+  const int32_t c = col[r];
+  if (c >= 0 && c < nnz) pos[c] = (int32_t)r;
+}
+
 template <typename T>
 cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32_t *hex, const int8_t *ply,
                         const double *X, const double *d, const void *history, const int32_t *row,
@@ -122,6 +133,12 @@ cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32
                                                 history ? nullptr : reinterpret_cast<T *>(base + kOffHin), nh * 8);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  int32_t *pos = reinterpret_cast<int32_t *>(base + kOffPos);
+  const int64_t nnz = nh * 8;
+  k_noalloc_pos<<<(int)((nnz + kBlock - 1) / kBlock), kBlock, 0, s>>>(col, pos, nnz);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  D.pos = pos;
   return launch_pass<T>(D, M, s, kBlock, nullptr);
 }
 
