@@ -500,14 +500,12 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   // --- device arena ---------------------------------------------------------
   const bool fp64 = ctx->precision == PDN_FP64;
   const size_t ts = fp64 ? 8 : 4;
-  const int n_part = grid_of(nn, kGatherBlock);
   struct Ptrs {
     int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
     uint8_t *nflag, *act[2], *rel, *pflag[2], *cflag[2];
     double *Xs, *mass, *d[2], *v[2], *nrm, *lam, *trial, *fhist, *fout;
-    Partial *part;
     Ctl *ctl;
     Striker *imp;
     StrikerStep *imp_step;
@@ -536,7 +534,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       P.u4[b] = A.take<char>(ts * 4 * nn);
       P.hist[b] = A.take<char>(ts * 7 * 8 * nh);
       P.rD[b] = A.take<char>(ts * 4 * nc1);
-      P.act[b] = A.take<uint8_t>(ns1);
+      P.act[b] = A.take<uint8_t>((ns1 + 15) & ~int64_t(15));  // read in 16-byte words by the tail
       P.pflag[b] = A.take<uint8_t>(nh);
       P.cflag[b] = A.take<uint8_t>(nc1);
     }
@@ -545,7 +543,6 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     P.nrm = A.take<double>(sizeof(double) * 3 * ns1);
     P.lam = A.take<double>(sizeof(double) * ns1);
     P.trial = A.take<double>(sizeof(double) * 6 * ns1);
-    P.part = A.take<Partial>(sizeof(Partial) * n_part);
     P.ctl = A.take<Ctl>(sizeof(Ctl));
     P.imp = A.take<Striker>(sizeof(Striker));
     P.imp_step = A.take<StrikerStep>(sizeof(StrikerStep));
@@ -573,7 +570,6 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   double *d_d[2] = {P.d[0], P.d[1]}, *d_v[2] = {P.v[0], P.v[1]};
   char *d_u4[2] = {P.u4[0], P.u4[1]}, *d_hist[2] = {P.hist[0], P.hist[1]}, *d_rD[2] = {P.rD[0], P.rD[1]};
   uint8_t *d_act[2] = {P.act[0], P.act[1]};
-  Partial *d_part = P.part;
   ctx->ctl_dev = P.ctl;
   ctx->imp_dev = P.imp;
   StrikerStep *d_imp_step = P.imp_step;
@@ -658,7 +654,6 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   chk(cudaMemset(d_rel, 0, std::max<int64_t>(ns, 1)));
   chk(cudaMemset(d_nrm, 0, sizeof(double) * 3 * std::max<int64_t>(ns, 1)));
   chk(cudaMemset(d_lam, 0, sizeof(double) * std::max<int64_t>(ns, 1)));
-  chk(cudaMemset(d_part, 0, sizeof(Partial) * n_part));
   Ctl c0{};
   c0.mode = MODE_DONE;
   c0.max_repeats = ctx->max_repeats;
@@ -712,8 +707,6 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     D.nrm = d_nrm;
     D.lam = d_lam;
     D.trial = d_trial;
-    D.part = d_part;
-    D.n_part = n_part;
     D.ctl = ctx->ctl_dev;
     D.imp = ctx->imp_dev;
     D.imp_step = d_imp_step;

@@ -34,6 +34,8 @@ struct Ctl {
   int64_t hist_count;  // contact-force samples written
   double time;
   double f_peak;
+  int32_t nonfinite;   // set by the gather when an acceleration is not finite
+  int32_t pad;
 };
 
 // Rigid striker (Sec. 2.2.2).  The committed part is written only by the tail
@@ -52,12 +54,6 @@ struct Striker {
 // over it; written by the contact kernel, read by gather and tail.
 struct StrikerStep {
   double c[3], w[3], aI[3];
-};
-
-// Per-block partial results of the gather (deterministic second-pass sum).
-struct Partial {
-  double f[3];
-  int32_t n_act, n_adh, nonfinite, pad;
 };
 
 constexpr int kMaxPlies = 64;
@@ -133,9 +129,7 @@ struct Dev {
   double *nrm;             // [3][ns]
   double *lam;             // [ns]
   double *trial;           // [6][ns] pre-projection d and v of active nodes
-  // reductions and control
-  Partial *part;           // [gather blocks]
-  int32_t n_part;
+  // control
   Ctl *ctl;
   Striker *imp;
   StrikerStep *imp_step;

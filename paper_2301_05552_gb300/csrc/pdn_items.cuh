@@ -1,7 +1,7 @@
 // Per-item bodies of the step kernels (one contact-surface node, one hex8,
-// one interface element, one block of nodes for the gather, the tail of a
-// pass), shared by the per-pass kernels (pdn_kernels.cu) and the batched
-// persistent kernel (pdn_batch.cu).
+// one interface element, one node for the gather, the tail of a pass),
+// shared by the per-pass kernels (pdn_kernels.cu) and the batched persistent
+// kernel (pdn_batch.cu).
 #pragma once
 
 #include <cstdint>
@@ -439,34 +439,69 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
 }
 
 // ---------------------------------------------------------------------------
-// Tail of a pass (one block, after the gather).  Sums the gather
-// partials in a fixed order, then commits the step (contact force
-// F = sum lambda_j n_j to the striker, Sec. 2.2.2; step counter, history and
-// node-buffer parities, force history), or marks the step for repetition when
-// adhesive nodes were released (Algorithm 2: the MPI_MAX of kfl_reset becomes
-// this single-block decision), or halts.  On commit it also advances the
-// striker for the next pass (RK4 with the committed force).
+// Tail of a pass (one block, after the gather).  Sums the reactions of the
+// active contact nodes in surface order (each thread a contiguous range, then
+// a fixed tree), counts the adhesive ones, then commits the step (contact
+// force F = sum lambda_j n_j to the striker, Sec. 2.2.2; step counter,
+// history and node-buffer parities, force history), or marks the step for
+// repetition when adhesive nodes were released (Algorithm 2: the MPI_MAX of
+// kfl_reset becomes this single-block decision), or halts.  On commit it also
+// advances the striker for the next pass (RK4 with the committed force).
 template <typename T>
 __device__ void tail_block(const Dev<T> &D, int mode) {
   Ctl *ctl = D.ctl;
-  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-  int nact = 0, nadh = 0, nonfin = 0;
-  // Each thread sums its strided partials in index order.  Only blocks that
-  // held active contact nodes carry a non-zero force, and FP64 adds run at a
-  // small fraction of the integer rate on this part, so the doubles are
-  // touched only for those partials (the counts decide, in integer).
-#pragma unroll 4
-  for (int k = threadIdx.x; k < D.n_part; k += blockDim.x) {
-    const Partial &pk = D.part[k];
-    const int na = pk.n_act;
-    if (na > 0) {
-      f0 += pk.f[0];
-      f1 += pk.f[1];
-      f2 += pk.f[2];
+  // the control block and the striker are read once, early, into registers;
+  // the striker only by passes that can commit a step (an internal-force
+  // evaluation may have no striker at all: D.imp is then null)
+  const bool stepping = (mode == MODE_ADVANCE || mode == MODE_REPEAT);
+  Ctl c;
+  Striker S;
+  StrikerStep ss;
+  if (threadIdx.x == 0) {
+    c = *ctl;
+    if (stepping) {
+      S = *D.imp;
+      ss = *D.imp_step;
     }
-    nact += na;
-    nadh += pk.n_adh;
-    nonfin |= pk.nonfinite;
+  }
+  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+  int nact = 0, nadh = 0;
+  if (stepping) {
+    const int64_t ns = D.ns;
+    const int spar = (int)((ctl->step + 1) & 1);
+    const uint8_t *act = D.act[spar];
+    // contiguous ranges of whole 16-flag words per thread (the flag arrays
+    // are 256-byte aligned and sized to a multiple of 16 bytes); the words
+    // are loaded together and only the rare set flags lead to further loads
+    const int64_t words = (ns + 15) / 16;
+    const int64_t per = (words + blockDim.x - 1) / blockDim.x;
+    const int64_t w0 = (int64_t)threadIdx.x * per;
+    const int64_t w1 = w0 + per < words ? w0 + per : words;
+    const uint4 *aw = reinterpret_cast<const uint4 *>(act);
+    for (int64_t wi = w0; wi < w1; wi += 4) {
+      uint4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = (wi + u < w1) ? aw[wi + u] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if ((q[u].x | q[u].y | q[u].z | q[u].w) == 0u) continue;
+        const uint32_t part[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+        for (int b = 0; b < 16; ++b) {
+          if (!((part[b >> 2] >> (8 * (b & 3))) & 0xffu)) continue;
+          const int64_t s = (wi + u) * 16 + b;
+          if (s >= ns) continue;
+          const double lam = D.lam[s];
+          if (lam < 0.0) {
+            ++nadh;
+          } else {
+            ++nact;
+            f0 += lam * D.nrm[s];
+            f1 += lam * D.nrm[ns + s];
+            f2 += lam * D.nrm[2 * ns + s];
+          }
+        }
+      }
+    }
   }
   const bool warp_has_force = __any_sync(0xffffffffu, nact > 0);
   if (warp_has_force) {
@@ -481,10 +516,9 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
   for (int o = 16; o > 0; o >>= 1) {
     nact += __shfl_xor_sync(0xffffffffu, nact, o);
     nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
-    nonfin |= __shfl_xor_sync(0xffffffffu, nonfin, o);
   }
   __shared__ double tf[3][32];
-  __shared__ int ti[3][32];
+  __shared__ int ti[2][32];
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
     tf[0][w] = f0;
@@ -492,16 +526,11 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     tf[2][w] = f2;
     ti[0][w] = nact;
     ti[1][w] = nadh;
-    ti[2][w] = nonfin;
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  // The control block and the striker are read into registers once and
-  // written back once: through pointers every field access would be a
-  // separate dependent global round trip.
-  Ctl c = *ctl;
   double F[3] = {0.0, 0.0, 0.0};
-  int na = 0, nd = 0, nf = 0;
+  int na = 0, nd = 0;
   for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
     if (ti[0][k] > 0) {
       F[0] += tf[0][k];
@@ -510,8 +539,9 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     }
     na += ti[0][k];
     nd += ti[1][k];
-    nf |= ti[2][k];
   }
+  const int nf = *(volatile int *)&ctl->nonfinite;
+  c.nonfinite = 0;  // for the next pass
   if (mode == MODE_FORCES) {
     c.mode = MODE_DONE;
   } else if (nf) {
@@ -531,8 +561,6 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     }
   } else {
     // commit step n+1
-    Striker S = *D.imp;
-    const StrikerStep ss = *D.imp_step;
     for (int i = 0; i < 3; ++i) {
       S.c[i] = ss.c[i];
       S.w[i] = ss.w[i];
@@ -564,18 +592,16 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
 // a = m^-1 (f^e - f^i) (Sec. 2.2.1), contact reaction of active nodes
 // lambda = m (a_I . n) - f . n with release of adhesive nodes (Eq. anodes,
 // Algorithm 2), and the Tchamwa-Wielgosz predictor of the next step:
-// v' = v + dt a, d' = d + dt v + phi dt^2 a.  One thread per node; per-block
-// reaction partial sums in a fixed tree order.
-// Called by every thread of a block: node j0 + threadIdx.x, block partial
-// written to D.part[part_index].
+// v' = v + dt a, d' = d + dt v + phi dt^2 a.  One thread per node.  The
+// contact reaction of an active node is stored per surface node (its sum is
+// the tail's job); a non-finite acceleration raises the pass's flag in the
+// control block.
 template <typename T>
-__device__ __forceinline__ void gather_items(const Dev<T> &D, int64_t j0, int64_t part_index, int mode) {
+__device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
   using V4 = typename Vec4T<T>::type;
-  const Ctl *ctl = D.ctl;
-  const int64_t j = j0 + threadIdx.x;
+  Ctl *ctl = D.ctl;
   const int64_t nn = D.nn;
-  double pf0 = 0.0, pf1 = 0.0, pf2 = 0.0;
-  int nact = 0, nadh = 0, nonfin = 0;
+  int nonfin = 0;
   if (j < nn) {
     T fx = T(0), fy = T(0), fz = T(0);
     const int r0 = D.row[j], r1 = D.row[j + 1];
@@ -613,15 +639,10 @@ __device__ __forceinline__ void gather_items(const Dev<T> &D, int64_t j0, int64_
           D.lam[s] = lam;
           if (lam < 0.0) {
             D.rel[s] = 1;
-            nadh = 1;
             a[0] = fr[0] / m;
             a[1] = fr[1] / m;
             a[2] = fr[2] / m;
           } else {
-            nact = 1;
-            pf0 = lam * n[0];
-            pf1 = lam * n[1];
-            pf2 = lam * n[2];
 #pragma unroll
             for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
           }
@@ -667,53 +688,8 @@ __device__ __forceinline__ void gather_items(const Dev<T> &D, int64_t j0, int64_
       D.u4[nxt][j] = u;
     }
   }
-  // block partials (fixed order: warp butterfly, then warps in index order)
-  __shared__ double sf[3][8];
-  __shared__ int si[3][8];
-  const int any = __syncthreads_or(nact | nadh | nonfin);
-  if (any) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      pf0 += __shfl_xor_sync(0xffffffffu, pf0, o);
-      pf1 += __shfl_xor_sync(0xffffffffu, pf1, o);
-      pf2 += __shfl_xor_sync(0xffffffffu, pf2, o);
-      nact += __shfl_xor_sync(0xffffffffu, nact, o);
-      nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
-      nonfin |= __shfl_xor_sync(0xffffffffu, nonfin, o);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-      sf[0][w] = pf0;
-      sf[1][w] = pf1;
-      sf[2][w] = pf2;
-      si[0][w] = nact;
-      si[1][w] = nadh;
-      si[2][w] = nonfin;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Partial p;
-      p.f[0] = p.f[1] = p.f[2] = 0.0;
-      p.n_act = p.n_adh = p.nonfinite = p.pad = 0;
-      const int nw = blockDim.x >> 5;
-      for (int k = 0; k < nw; ++k) {
-        p.f[0] += sf[0][k];
-        p.f[1] += sf[1][k];
-        p.f[2] += sf[2][k];
-        p.n_act += si[0][k];
-        p.n_adh += si[1][k];
-        p.nonfinite |= si[2][k];
-      }
-      D.part[part_index] = p;
-    }
-  } else if (threadIdx.x == 0) {
-    Partial p;
-    p.f[0] = p.f[1] = p.f[2] = 0.0;
-    p.n_act = p.n_adh = p.nonfinite = p.pad = 0;
-    D.part[part_index] = p;
-  }
+  if (nonfin) atomicOr(&ctl->nonfinite, 1);
 }
-
 
 }  // namespace detail
 }  // namespace pdn

@@ -51,7 +51,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  gather_items(D, (int64_t)blockIdx.x * blockDim.x, (int64_t)blockIdx.x, mode);
+  gather_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 // Kernel 5: the tail of a pass as its own small launch (kept out of the

@@ -8,7 +8,7 @@
 // its steady state.  They cannot create a pdn context (pdn_init_mesh
 // allocates).  This entry point takes every input and the output as caller
 // buffers and keeps its working memory (mirrors, element forces, trial
-// history, per-block partials, control block) in one file-scope __device__
+// history, control block) in one file-scope __device__
 // array of fixed size, so it allocates nothing.
 //
 // The scratch array lives on every device that loads this library until the
@@ -38,13 +38,11 @@ constexpr int kMaxDevices = 64;
 // Byte sizes of the scratch regions at the maxima, FP64 element precision
 // (the larger of the two).
 constexpr size_t kCtlBytes = 256;
-constexpr size_t kPartBytes = ((PDN_NOALLOC_MAX_NODES + kBlock - 1) / kBlock) * sizeof(Partial);
 constexpr size_t kNodeV4Bytes = (size_t)PDN_NOALLOC_MAX_NODES * 32;
 constexpr size_t kHistBytes = (size_t)PDN_NOALLOC_MAX_HEX * 8 * 7 * 8;
 constexpr size_t kFeBytes = (size_t)PDN_NOALLOC_MAX_HEX * 8 * 32;
 constexpr size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
-constexpr size_t kOffPart = round256(kCtlBytes);
-constexpr size_t kOffX4 = kOffPart + round256(kPartBytes);
+constexpr size_t kOffX4 = round256(kCtlBytes);
 constexpr size_t kOffU4 = kOffX4 + round256(kNodeV4Bytes);
 constexpr size_t kOffHin = kOffU4 + round256(kNodeV4Bytes);
 constexpr size_t kOffHout = kOffHin + round256(kHistBytes);
@@ -123,8 +121,6 @@ cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32
   D.hist[0] = hin;
   D.hist[1] = reinterpret_cast<T *>(base + kOffHout);
   D.fe = reinterpret_cast<V4 *>(base + kOffFe);
-  D.part = reinterpret_cast<Partial *>(base + kOffPart);
-  D.n_part = (int32_t)((nn + kBlock - 1) / kBlock);
   D.ctl = reinterpret_cast<Ctl *>(base);
   D.fout = f_int;
   const int64_t work = std::max<int64_t>(nn, 1);
