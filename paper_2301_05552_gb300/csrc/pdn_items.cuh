@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pdn.h"
 #include "pdn_device.cuh"
@@ -114,6 +115,210 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
 }
 
 // ---------------------------------------------------------------------------
+// Packed FP32 pairs: one sm_100-family instruction computes both lanes, each
+// lane rounded exactly as the scalar operation.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Gauss point of lane l (0: xi < 0, 1: xi > 0) in xi-pair p (bit 0: eta > 0,
+// bit 1: zeta > 0), in the point numbering of the node signs (sgn_x/y/z).
+__host__ __device__ constexpr int pair_point(int p, int l) {
+  return ((p >> 1) << 2) + ((p & 1) ? (l ? 2 : 3) : (l ? 1 : 0));
+}
+
+// The FP32 hex8 of an axis-aligned box, two Gauss points per step.  The two
+// points of a pair differ only in the sign of xi, so the displacement
+// gradient, the Green strain, both rotations, P = S F^T and the mode-space
+// force sums run as packed pairs; the intralaminar law runs per point.
+// Same formulation as the scalar element below (Eq. fcont, Algorithm 4).
+__device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode) {
+  using V4 = float4;
+  const Ctl *ctl = D.ctl;
+  if (e >= D.nh) return;
+  const int64_t nh = D.nh;
+  const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+  const int hb = ctl->hpar;
+  const V4 *__restrict__ U = D.u4[ub];
+  const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
+  const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
+  const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const float *__restrict__ hin = D.hist[hb] + e;
+  float *__restrict__ hout = D.hist[hb ^ 1] + e;
+  const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][e] != 0;
+  bool dirty = false;
+  float bm[8][3];
+  float jd[3], wd[3], vol;
+  {
+    float ua[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const V4 u = U[nd[a]];
+      ua[a][0] = u.x;
+      ua[a][1] = u.y;
+      ua[a][2] = u.z;
+    }
+    to_modes(ua, bm);
+    const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
+    const float J0 = 0.5f * (x6.x - x0.x), J1 = 0.5f * (x6.y - x0.y), J2 = 0.5f * (x6.z - x0.z);
+    const float det = J0 * (J1 * J2);
+    jd[0] = 1.0f / J0;
+    jd[1] = 1.0f / J1;
+    jd[2] = 1.0f / J2;
+    wd[0] = det * jd[0];
+    wd[1] = det * jd[1];
+    wd[2] = det * jd[2];
+    vol = 8.0f * det;
+  }
+  const int ply = D.ply[e];
+  const float cs = M.ply_c[ply], sn = M.ply_s[ply];
+  const float c2 = cs * cs, s2 = sn * sn, csn = cs * sn;
+  const ElemLaw<float> L = elem_law(M, e);
+  float lc = -1.0f;
+  // mode-space force sums
+  float C[8][3];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) C[m][0] = C[m][1] = C[m][2] = 0.0f;
+  const float gp = 0.57735026918962576451f;
+  const float2 xi = make_float2(-gp, gp);
+#pragma unroll 1
+  for (int p = 0; p < 4; ++p) {
+    const int gx = pair_point(p, 0), gy = pair_point(p, 1);
+    // the pair's history, in flight while the strains are computed
+    float2 h[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f)
+      h[f] = pristine_in ? p2(f < 4 ? 1.0f : 0.0f)
+                         : make_float2(hin[(int64_t)(f * 8 + gx) * nh], hin[(int64_t)(f * 8 + gy) * nh]);
+    const float et = (p & 1) ? gp : -gp, ze = (p & 2) ? gp : -gp;
+    const float etze = et * ze;
+    // H = du/dX: the xi column is the same in both lanes; the eta and zeta
+    // columns are a + xi b
+    float2 H[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      H[i][0] = p2((bm[1][i] + et * bm[4][i] + ze * bm[6][i] + etze * bm[7][i]) * jd[0]);
+      const float a1 = (bm[2][i] + ze * bm[5][i]) * jd[1], b1 = (bm[4][i] + ze * bm[7][i]) * jd[1];
+      const float a2 = (bm[3][i] + et * bm[5][i]) * jd[2], b2 = (bm[6][i] + et * bm[7][i]) * jd[2];
+      H[i][1] = pfma(xi, p2(b1), p2(a1));
+      H[i][2] = pfma(xi, p2(b2), p2(a2));
+    }
+    // Green strain E = 1/2 (H + H^T + H^T H), then to ply axes (rotation about z)
+    float2 E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = i; k < 3; ++k) {
+        float2 t = padd(H[i][k], H[k][i]);
+        t = pfma(H[0][i], H[0][k], t);
+        t = pfma(H[1][i], H[1][k], t);
+        t = pfma(H[2][i], H[2][k], t);
+        E[i][k] = pmul(p2(0.5f), t);
+      }
+    float2 ep[6];
+    ep[0] = pfma(p2(s2), E[1][1], pfma(p2(2.0f * csn), E[0][1], pmul(p2(c2), E[0][0])));
+    ep[1] = pfma(p2(c2), E[1][1], pfma(p2(-2.0f * csn), E[0][1], pmul(p2(s2), E[0][0])));
+    ep[2] = E[2][2];
+    ep[3] = pfma(p2(2.0f * csn), E[1][1], pfma(p2(2.0f * (c2 - s2)), E[0][1], pmul(p2(-2.0f * csn), E[0][0])));
+    ep[4] = pfma(p2(2.0f * sn), E[1][2], pmul(p2(2.0f * cs), E[0][2]));
+    ep[5] = pfma(p2(2.0f * cs), E[1][2], pmul(p2(-2.0f * sn), E[0][2]));
+    // the law, one point at a time
+    float2 sm[6];
+    {
+      float el[6], hl[7], sl[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) el[k] = ep[k].x;
+#pragma unroll
+      for (int f = 0; f < 7; ++f) hl[f] = h[f].x;
+      cdm(M, L, (const float(*)[3]) nullptr, vol, lc, el, hl, sl);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sm[k].x = sl[k];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) h[f].x = hl[f];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) el[k] = ep[k].y;
+#pragma unroll
+      for (int f = 0; f < 7; ++f) hl[f] = h[f].y;
+      cdm(M, L, (const float(*)[3]) nullptr, vol, lc, el, hl, sl);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sm[k].y = sl[k];
+#pragma unroll
+      for (int f = 0; f < 7; ++f) h[f].y = hl[f];
+    }
+    if (!pristine_in) {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) {
+        hout[(int64_t)(f * 8 + gx) * nh] = h[f].x;
+        hout[(int64_t)(f * 8 + gy) * nh] = h[f].y;
+      }
+    } else {
+      const bool changed = h[0].x > 1.0f || h[1].x > 1.0f || h[2].x > 1.0f || h[3].x > 1.0f || h[4].x != 0.0f ||
+                           h[5].x != 0.0f || h[6].x != 0.0f || h[0].y > 1.0f || h[1].y > 1.0f ||
+                           h[2].y > 1.0f || h[3].y > 1.0f || h[4].y != 0.0f || h[5].y != 0.0f || h[6].y != 0.0f;
+      if (changed && !dirty) {
+        // first change in a pristine element: the points of the earlier
+        // pairs keep the initial history, not yet in the output buffer
+        for (int q = 0; q < p; ++q)
+#pragma unroll
+          for (int f = 0; f < 7; ++f) {
+            hout[(int64_t)(f * 8 + pair_point(q, 0)) * nh] = f < 4 ? 1.0f : 0.0f;
+            hout[(int64_t)(f * 8 + pair_point(q, 1)) * nh] = f < 4 ? 1.0f : 0.0f;
+          }
+        dirty = true;
+      }
+      if (dirty) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) {
+          hout[(int64_t)(f * 8 + gx) * nh] = h[f].x;
+          hout[(int64_t)(f * 8 + gy) * nh] = h[f].y;
+        }
+      }
+    }
+    // back to global axes: S = R Sm R^T
+    float2 S[3][3];
+    S[0][0] = pfma(p2(s2), sm[1], pfma(p2(-2.0f * csn), sm[3], pmul(p2(c2), sm[0])));
+    S[1][1] = pfma(p2(c2), sm[1], pfma(p2(2.0f * csn), sm[3], pmul(p2(s2), sm[0])));
+    S[2][2] = sm[2];
+    S[0][1] = S[1][0] = pfma(p2(-csn), sm[1], pfma(p2(c2 - s2), sm[3], pmul(p2(csn), sm[0])));
+    S[0][2] = S[2][0] = pfma(p2(-sn), sm[5], pmul(p2(cs), sm[4]));
+    S[1][2] = S[2][1] = pfma(p2(cs), sm[5], pmul(p2(sn), sm[4]));
+    // P = S F^T with F = I + H
+    float2 P[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        P[i][k] = pfma(S[i][2], H[k][2], pfma(S[i][1], H[k][1], pfma(S[i][0], H[k][0], S[i][k])));
+    // mode sums of Q_k = w_k P_k (w_k = det J / J_kk) times the Gauss-point
+    // values of the mode derivatives; the lanes enter through their sum
+    // (xi-even modes) and difference (xi-odd modes)
+    const float e0 = et * wd[0], z1 = ze * wd[1], e2 = et * wd[2], z0 = ze * wd[0], ez0 = etze * wd[0];
+    const float g1 = gp * wd[1], g2 = gp * wd[2], gz1 = g1 * ze, ge2 = g2 * et;
+#pragma unroll
+    for (int I = 0; I < 3; ++I) {
+      const float s0 = P[0][I].x + P[0][I].y, s1 = P[1][I].x + P[1][I].y, s2s = P[2][I].x + P[2][I].y;
+      const float d1 = P[1][I].y - P[1][I].x, d2 = P[2][I].y - P[2][I].x;
+      C[1][I] += wd[0] * s0;
+      C[2][I] += wd[1] * s1;
+      C[3][I] += wd[2] * s2s;
+      C[4][I] += e0 * s0 + g1 * d1;
+      C[5][I] += z1 * s1 + e2 * s2s;
+      C[6][I] += z0 * s0 + g2 * d2;
+      C[7][I] += ez0 * s0 + gz1 * d1 + ge2 * d2;
+    }
+  }
+  if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
+  float f[8][3];
+  from_modes(C, f);
+  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e);
+  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e + 1);
+  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
+}
+
+// ---------------------------------------------------------------------------
 // Kernel 2: hex8 internal forces, total Lagrangian, 2x2x2 Gauss (Sec. 2,
 // Eq. fcont), with the intralaminar law per Gauss point.  One thread per
 // element; geometry and displacement enter through their trilinear modes, so
@@ -125,6 +330,10 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
 // The next Gauss point's history is loaded while the current one computes.
 template <typename T, bool BOX>
 __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64_t e, int mode) {
+  if constexpr (BOX && std::is_same<T, float>::value) {
+    hex_item_box_pairs(D, M, e, mode);
+    return;
+  }
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
   if (e >= D.nh) return;
