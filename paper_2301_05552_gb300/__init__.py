@@ -26,6 +26,8 @@ __all__ = [
     "pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
     "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
     "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
+    "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
+    "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
     "PDN_FP64", "PDN_FP32_FORCE", "FIELDS", "KERNELS",
 ]
 
@@ -37,7 +39,9 @@ ERRORS = {-1: "PDN_E_ARG", -2: "PDN_E_CUDA", -3: "PDN_E_OOM", -4: "PDN_E_NONFINI
           -5: "PDN_E_RELEASE_LIMIT", -6: "PDN_E_TIMEOUT", -7: "PDN_E_UNSTABLE", -8: "PDN_E_STATE"}
 EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
            "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
-           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc"]
+           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
+           "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
+           "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error"]
 
 
 class PdnError(RuntimeError):
@@ -75,6 +79,15 @@ class Info(C.Structure):
                 ("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
                 ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32),
                 ("hex_variant", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double * 4)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_plates", C.c_int32), ("precision", C.c_int32), ("status", C.c_int32), ("tuned", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("tile_items", C.c_int32), ("reg_variant", C.c_int32),
+                ("grid", C.c_int32), ("graph", C.c_int32), ("n_candidates", C.c_int32),
+                ("n_tiles", C.c_int64 * 4), ("launches", C.c_int64), ("passes", C.c_int64),
+                ("tune_ms", C.c_double * 16), ("tune_bps", C.c_int32 * 16), ("tune_tile", C.c_int32 * 16),
+                ("tune_var", C.c_int32 * 16)]
 
 
 _lock = threading.Lock()
@@ -117,6 +130,19 @@ def lib():
                                                      C.POINTER(Material), dp, C.c_int32, C.c_int32, C.c_int32,
                                                      C.c_int32, vp, vp]
             L.pdn_internal_force_noalloc.restype = C.c_int
+            L.pdn_batch_init.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(MeshDesc), C.POINTER(Material),
+                                         C.POINTER(Options)]
+            L.pdn_batch_plate.argtypes = [vp, C.c_int32]
+            L.pdn_batch_plate.restype = vp
+            L.pdn_batch_step.argtypes = [vp, C.c_int64]
+            L.pdn_batch_get_info.argtypes = [vp, C.POINTER(BatchInfo)]
+            L.pdn_batch_test_barrier_timeout.argtypes = [vp, C.c_double]
+            L.pdn_batch_destroy.argtypes = [vp]
+            L.pdn_batch_destroy.restype = None
+            L.pdn_batch_last_error.argtypes = [vp]
+            L.pdn_batch_last_error.restype = C.c_char_p
+            for name in ("pdn_batch_init", "pdn_batch_step", "pdn_batch_get_info", "pdn_batch_test_barrier_timeout"):
+                getattr(L, name).restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
                          "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
                          "pdn_init_mesh"):
@@ -139,15 +165,16 @@ def _check(ctx, rc):
 class Context:
     """A pdn_ctx handle (one plate + one striker on the current device)."""
 
-    def __init__(self, handle, n_nodes, n_hex, n_coh, n_surf, stream):
+    def __init__(self, handle, n_nodes, n_hex, n_coh, n_surf, stream, owner=None):
         self.handle = handle
         self.n_nodes, self.n_hex, self.n_coh, self.n_surf = n_nodes, n_hex, n_coh, n_surf
         self.stream = stream
+        self.owner = owner  # a Batch owns the contexts of its plates
 
     def close(self):
-        if self.handle:
+        if self.handle and self.owner is None:
             lib().pdn_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -166,14 +193,10 @@ def _current_stream():
     return None
 
 
-def pdn_init_mesh(plate, material: dict, precision: int = PDN_FP32_FORCE, damage_on: bool = True,
-                  plasticity_on: bool = True, max_release_iters: int = 8, phi: float = 1.0, dt: float = 0.0,
-                  dt_safety: float = 0.5, gravity=(0.0, 0.0, 0.0), history_cap: int = 1 << 20,
-                  stream: Optional[int] = None) -> Context:
-    """pdn_init_mesh: ``plate`` is any object with the fields of
-    pdn_inputs.Plate (X [3,n], hex [n,8], coh [m,8], ply_of_hex, ply_angle_deg,
-    fixed, surf)."""
-    L = lib()
+def _mesh_desc(plate):
+    """MeshDesc of a plate (any object with the fields of pdn_inputs.Plate:
+    X [3,n], hex [n,8], coh [m,8], ply_of_hex, ply_angle_deg, fixed, surf)
+    and the arrays it points into (keep them alive while it is used)."""
     keep = dict(
         X=np.ascontiguousarray(plate.X, dtype=np.float64),
         hex=np.ascontiguousarray(plate.hex, dtype=np.int32).reshape(-1, 8),
@@ -196,19 +219,43 @@ def pdn_init_mesh(plate, material: dict, precision: int = PDN_FP32_FORCE, damage
     m.n_plies = keep["ang"].shape[0]
     m.fixed = _ptr(keep["fixed"], C.c_uint8)
     m.surf = _ptr(keep["surf"], C.c_int32) if m.n_surf else None
+    return m, keep
+
+
+def _material(material: dict) -> Material:
     mat = Material()
     for k in MATERIAL_KEYS:
         setattr(mat, k, float(material[k]))
     mat.seed = int(material["seed"])
+    return mat
+
+
+def _options(precision, damage_on, plasticity_on, max_release_iters, phi, dt, dt_safety, gravity,
+             history_cap, stream) -> Options:
     o = Options()
     o.precision, o.damage_on, o.plasticity_on = int(precision), int(damage_on), int(plasticity_on)
     o.max_release_iters, o.phi, o.dt, o.dt_safety = int(max_release_iters), float(phi), float(dt), float(dt_safety)
     for i in range(3):
         o.gravity[i] = float(gravity[i])
     o.history_cap = int(history_cap)
+    o.stream = stream
+    return o
+
+
+def pdn_init_mesh(plate, material: dict, precision: int = PDN_FP32_FORCE, damage_on: bool = True,
+                  plasticity_on: bool = True, max_release_iters: int = 8, phi: float = 1.0, dt: float = 0.0,
+                  dt_safety: float = 0.5, gravity=(0.0, 0.0, 0.0), history_cap: int = 1 << 20,
+                  stream: Optional[int] = None) -> Context:
+    """pdn_init_mesh: ``plate`` is any object with the fields of
+    pdn_inputs.Plate (X [3,n], hex [n,8], coh [m,8], ply_of_hex, ply_angle_deg,
+    fixed, surf)."""
+    L = lib()
+    m, keep = _mesh_desc(plate)
+    mat = _material(material)
     if stream is None:
         stream = _current_stream()
-    o.stream = stream
+    o = _options(precision, damage_on, plasticity_on, max_release_iters, phi, dt, dt_safety, gravity,
+                 history_cap, stream)
     h = C.c_void_p()
     rc = L.pdn_init_mesh(C.byref(h), C.byref(m), C.byref(mat), C.byref(o))
     if rc < 0:
@@ -322,6 +369,105 @@ def pdn_internal_force_noalloc(n_nodes: int, n_hex: int, hex_dev, ply_dev, X_dev
                                           int(plasticity_on), ptr(f_out_dev), stream)
     if rc < 0:
         raise PdnError(rc, (lib().pdn_last_error(None) or b"").decode())
+
+
+class Batch:
+    """A pdn_batch handle: plates[p] are its (non-owning) plate contexts."""
+
+    def __init__(self, handle, plates, stream):
+        self.handle = handle
+        self.plates = plates
+        self.stream = stream
+
+    def close(self):
+        if self.handle:
+            for c in self.plates:
+                c.handle = None
+            lib().pdn_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _bcheck(b, rc):
+    if rc < 0:
+        msg = lib().pdn_batch_last_error(b.handle if b is not None else None)
+        raise PdnError(int(rc), (msg or b"").decode())
+    return rc
+
+
+def pdn_batch_init(plates, materials, precision: int = PDN_FP32_FORCE, damage_on: bool = True,
+                   plasticity_on: bool = True, max_release_iters: int = 8, phi: float = 1.0, dt: float = 0.0,
+                   dt_safety: float = 0.5, gravity=(0.0, 0.0, 0.0), history_cap: int = 1 << 20,
+                   stream: Optional[int] = None) -> Batch:
+    """pdn_batch_init: one plate per entry of ``plates`` (pdn_inputs.Plate
+    fields) with material dict ``materials[p]``; the options are common."""
+    L = lib()
+    n = len(plates)
+    descs = (MeshDesc * n)()
+    mats = (Material * n)()
+    keep = []
+    for p, (pl, mt) in enumerate(zip(plates, materials)):
+        m, k = _mesh_desc(pl)
+        keep.append(k)
+        descs[p] = m
+        mats[p] = _material(mt)
+    if stream is None:
+        stream = _current_stream()
+    o = _options(precision, damage_on, plasticity_on, max_release_iters, phi, dt, dt_safety, gravity,
+                 history_cap, stream)
+    h = C.c_void_p()
+    rc = L.pdn_batch_init(C.byref(h), n, descs, mats, C.byref(o))
+    if rc < 0:
+        raise PdnError(rc, (L.pdn_batch_last_error(None) or b"").decode())
+    b = Batch(h, [], stream)
+    for p in range(n):
+        ph = L.pdn_batch_plate(h, p)
+        d = descs[p]
+        b.plates.append(Context(C.c_void_p(ph), d.n_nodes, d.n_hex, d.n_coh, d.n_surf, stream, owner=b))
+    return b
+
+
+def pdn_batch_plate(b: Batch, p: int) -> Context:
+    return b.plates[p]
+
+
+def pdn_batch_step(b: Batch, nsteps: int):
+    _bcheck(b, lib().pdn_batch_step(b.handle, int(nsteps)))
+
+
+def pdn_batch_get_info(b: Batch) -> dict:
+    info = BatchInfo()
+    _bcheck(b, lib().pdn_batch_get_info(b.handle, C.byref(info)))
+    out = {k: getattr(info, k) for k, _ in BatchInfo._fields_}
+    nc = info.n_candidates
+    out["n_tiles"] = list(info.n_tiles)
+    out["candidates"] = [dict(ms=info.tune_ms[k], blocks_per_sm=info.tune_bps[k], tile_items=info.tune_tile[k],
+                              reg_variant=info.tune_var[k]) for k in range(nc)]
+    for k in ("tune_ms", "tune_bps", "tune_tile", "tune_var"):
+        out.pop(k)
+    return out
+
+
+def pdn_batch_test_barrier_timeout(b: Batch, timeout_ms: float) -> int:
+    """Returns the status code (PDN_E_TIMEOUT = -6 when the bounded wait ran
+    out as designed); does not raise for that code."""
+    rc = lib().pdn_batch_test_barrier_timeout(b.handle, float(timeout_ms))
+    if rc < 0 and rc != -6:
+        _bcheck(b, rc)
+    return int(rc)
+
+
+def pdn_batch_destroy(b: Batch):
+    b.close()
+
+
+def pdn_batch_last_error(b: Optional[Batch]) -> str:
+    return (lib().pdn_batch_last_error(b.handle if b is not None else None) or b"").decode()
 
 
 class Solver:

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "pdn.h"
+#include "pdn_context.h"
 #include "pdn_internal.h"
 
 using namespace pdn;
@@ -29,17 +30,6 @@ constexpr int kGatherBlock = 256;
 constexpr int kGraphPasses = 32;
 constexpr int kProfilePasses = 64;
 
-// Arena of device memory: one cudaMalloc, 256-byte aligned sub-allocations.
-struct Arena {
-  char *base = nullptr;
-  size_t size = 0, used = 0;
-  template <typename P>
-  P *take(size_t bytes) {
-    size_t off = (used + 255) & ~size_t(255);
-    used = off + bytes;
-    return base ? reinterpret_cast<P *>(base + off) : nullptr;
-  }
-};
 
 __global__ void k_fill_hist_float(float *h, int64_t per_field, int64_t n_init_fields) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -73,43 +63,6 @@ inline int grid_of(int64_t n, int b) {
 
 }  // namespace
 
-struct pdn_ctx {
-  int precision = PDN_FP32_FORCE;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int64_t nn = 0, nh = 0, nc = 0, ns = 0;
-  Arena arena;
-  Dev<float> Df{};
-  Dev<double> Dd{};
-  Mat<float> Mf{};
-  Mat<double> Md{};
-  Ctl *ctl_dev = nullptr;
-  Ctl *ctl_host = nullptr;  // pinned
-  Striker *imp_dev = nullptr;
-  float *field = nullptr;
-  double dt = 0, dt_bulk = 0, dt_coh = 0, phi = 1;
-  double grav[3] = {0, 0, 0};
-  int max_repeats = 8;
-  int64_t hist_cap = 0;
-  bool has_imp = false;
-  bool tuned = false;
-  float tune_ms[4] = {0, 0, 0, 0};  // mean hex time per variant (autotuner)
-  cudaGraphExec_t graph = nullptr;
-  // side stream for the interface kernel, forked from and joined back into
-  // the main stream inside every pass
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  std::vector<cudaEvent_t> prof_ev;
-  std::string err;
-
-  // Pointers common to both precisions.
-  template <typename F>
-  void both(F &&f) {
-    f(Df);
-    f(Dd);
-  }
-};
 
 namespace {
 
@@ -766,7 +719,7 @@ int autotune(pdn_ctx *ctx) {
   for (int k = 0; k < 6; ++k) PDN_CU(cudaEventCreate(&ev[k]), "tune event");
   int best = 0;
   float best_ms = 1e30f;
-  const int reps = 3;
+  const int reps = 8;
   for (int v = 0; v < nvar; ++v) {
     ctx->Df.hex_variant = v;
     float sum = 0.f;

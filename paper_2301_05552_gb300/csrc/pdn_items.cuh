@@ -673,74 +673,80 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
       ss = *D.imp_step;
     }
   }
-  double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-  int nact = 0, nadh = 0;
-  if (stepping) {
-    const int64_t ns = D.ns;
-    const int spar = (int)((ctl->step + 1) & 1);
-    const uint8_t *act = D.act[spar];
-    // contiguous ranges of whole 16-flag words per thread (the flag arrays
-    // are 256-byte aligned and sized to a multiple of 16 bytes); the words
-    // are loaded together and only the rare set flags lead to further loads
-    const int64_t words = (ns + 15) / 16;
-    const int64_t per = (words + blockDim.x - 1) / blockDim.x;
-    const int64_t w0 = (int64_t)threadIdx.x * per;
-    const int64_t w1 = w0 + per < words ? w0 + per : words;
-    const uint4 *aw = reinterpret_cast<const uint4 *>(act);
-    for (int64_t wi = w0; wi < w1; wi += 4) {
-      uint4 q[4];
+  // The surface is cut into kTailLanes contiguous ranges of 16-flag words,
+  // reduced in a fixed tree: xor-shuffles within each group of 32 ranges,
+  // then the groups in order.  A block of any size that divides kTailLanes
+  // (>= 32) plays the ranges as virtual threads, so the sum and its rounding
+  // do not depend on the launch shape.
+  constexpr int kTailLanes = 256;
+  __shared__ double tf[3][kTailLanes / 32];
+  __shared__ int ti[2][kTailLanes / 32];
+  const int64_t ns = D.ns;
+  const int64_t words = (ns + 15) / 16;
+  const int64_t per = (words + kTailLanes - 1) / kTailLanes;
+  const uint4 *aw = stepping ? reinterpret_cast<const uint4 *>(D.act[(int)((ctl->step + 1) & 1)]) : nullptr;
+  for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
+    const int v = v0 + (int)threadIdx.x;  // virtual thread
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    int nact = 0, nadh = 0;
+    if (stepping) {
+      // the flag arrays are 256-byte aligned and sized to a multiple of 16
+      // bytes; the words are loaded together and only the rare set flags
+      // lead to further loads
+      const int64_t w0 = (int64_t)v * per;
+      const int64_t w1 = w0 + per < words ? w0 + per : words;
+      for (int64_t wi = w0; wi < w1; wi += 4) {
+        uint4 q[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) q[u] = (wi + u < w1) ? aw[wi + u] : make_uint4(0u, 0u, 0u, 0u);
+        for (int u = 0; u < 4; ++u) q[u] = (wi + u < w1) ? aw[wi + u] : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if ((q[u].x | q[u].y | q[u].z | q[u].w) == 0u) continue;
-        const uint32_t part[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-        for (int b = 0; b < 16; ++b) {
-          if (!((part[b >> 2] >> (8 * (b & 3))) & 0xffu)) continue;
-          const int64_t s = (wi + u) * 16 + b;
-          if (s >= ns) continue;
-          const double lam = D.lam[s];
-          if (lam < 0.0) {
-            ++nadh;
-          } else {
-            ++nact;
-            f0 += lam * D.nrm[s];
-            f1 += lam * D.nrm[ns + s];
-            f2 += lam * D.nrm[2 * ns + s];
+        for (int u = 0; u < 4; ++u) {
+          if ((q[u].x | q[u].y | q[u].z | q[u].w) == 0u) continue;
+          const uint32_t part[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+          for (int b = 0; b < 16; ++b) {
+            if (!((part[b >> 2] >> (8 * (b & 3))) & 0xffu)) continue;
+            const int64_t s = (wi + u) * 16 + b;
+            if (s >= ns) continue;
+            const double lam = D.lam[s];
+            if (lam < 0.0) {
+              ++nadh;
+            } else {
+              ++nact;
+              f0 += lam * D.nrm[s];
+              f1 += lam * D.nrm[ns + s];
+              f2 += lam * D.nrm[2 * ns + s];
+            }
           }
         }
       }
     }
-  }
-  const bool warp_has_force = __any_sync(0xffffffffu, nact > 0);
-  if (warp_has_force) {
+    if (__any_sync(0xffffffffu, nact > 0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        f0 += __shfl_xor_sync(0xffffffffu, f0, o);
+        f1 += __shfl_xor_sync(0xffffffffu, f1, o);
+        f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      f0 += __shfl_xor_sync(0xffffffffu, f0, o);
-      f1 += __shfl_xor_sync(0xffffffffu, f1, o);
-      f2 += __shfl_xor_sync(0xffffffffu, f2, o);
+      nact += __shfl_xor_sync(0xffffffffu, nact, o);
+      nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
     }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nact += __shfl_xor_sync(0xffffffffu, nact, o);
-    nadh += __shfl_xor_sync(0xffffffffu, nadh, o);
-  }
-  __shared__ double tf[3][32];
-  __shared__ int ti[2][32];
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
-    tf[0][w] = f0;
-    tf[1][w] = f1;
-    tf[2][w] = f2;
-    ti[0][w] = nact;
-    ti[1][w] = nadh;
+    if ((threadIdx.x & 31) == 0) {
+      const int g = v >> 5;
+      tf[0][g] = f0;
+      tf[1][g] = f1;
+      tf[2][g] = f2;
+      ti[0][g] = nact;
+      ti[1][g] = nadh;
+    }
   }
   __syncthreads();
   if (threadIdx.x != 0) return;
   double F[3] = {0.0, 0.0, 0.0};
   int na = 0, nd = 0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+  for (int k = 0; k < kTailLanes / 32; ++k) {
     if (ti[0][k] > 0) {
       F[0] += tf[0][k];
       F[1] += tf[1][k];
@@ -805,99 +811,107 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
 // contact reaction of an active node is stored per surface node (its sum is
 // the tail's job); a non-finite acceleration raises the pass's flag in the
 // control block.
+//
+// gather_node: node j (< nn), given the sum of its element forces in CSR order.
 template <typename T>
-__device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
+__device__ __forceinline__ void gather_node(const Dev<T> &D, int64_t j, int mode, T fx, T fy, T fz) {
   using V4 = typename Vec4T<T>::type;
   Ctl *ctl = D.ctl;
   const int64_t nn = D.nn;
   int nonfin = 0;
-  if (j < nn) {
-    T fx = T(0), fy = T(0), fz = T(0);
-    const int r0 = D.row[j], r1 = D.row[j + 1];
-    // the node's element forces are contiguous (written at their CSR
-    // positions); summed in CSR order: hexes, then interfaces, ascending
-#pragma unroll 4
-    for (int r = r0; r < r1; ++r) {
-      const V4 f = D.fe[r];
-      fx += f.x;
-      fy += f.y;
-      fz += f.z;
-    }
-    if (mode == MODE_FORCES) {
-      D.fout[j] = (double)fx;
-      D.fout[nn + j] = (double)fy;
-      D.fout[2 * nn + j] = (double)fz;
-    } else {
-      const int cur = ctl->dpar, nxt = cur ^ 1;
-      const uint8_t fl = D.nflag[j];
-      double a[3];
-      bool done = false;
-      if ((fl & 8) && mode != MODE_PRIME) {
-        const int64_t s = D.surf_of[j];
-        const int spar = (int)((ctl->step + 1) & 1);
-        if (D.act[spar][s]) {
-          const int64_t ns = D.ns;
-          const double m = D.mass[j];
-          const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
-          const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy,
-                                m * D.grav[2] - (double)fz};
-          const StrikerStep *ss = D.imp_step;
-          const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
-          const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
-          const double lam = m * adot - fdot;
-          D.lam[s] = lam;
-          if (lam < 0.0) {
-            D.rel[s] = 1;
-            a[0] = fr[0] / m;
-            a[1] = fr[1] / m;
-            a[2] = fr[2] / m;
-          } else {
+  if (mode == MODE_FORCES) {
+    D.fout[j] = (double)fx;
+    D.fout[nn + j] = (double)fy;
+    D.fout[2 * nn + j] = (double)fz;
+  } else {
+    const int cur = ctl->dpar, nxt = cur ^ 1;
+    const uint8_t fl = D.nflag[j];
+    double a[3];
+    bool done = false;
+    if ((fl & 8) && mode != MODE_PRIME) {
+      const int64_t s = D.surf_of[j];
+      const int spar = (int)((ctl->step + 1) & 1);
+      if (D.act[spar][s]) {
+        const int64_t ns = D.ns;
+        const double m = D.mass[j];
+        const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
+        const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy,
+                              m * D.grav[2] - (double)fz};
+        const StrikerStep *ss = D.imp_step;
+        const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
+        const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
+        const double lam = m * adot - fdot;
+        D.lam[s] = lam;
+        if (lam < 0.0) {
+          D.rel[s] = 1;
+          a[0] = fr[0] / m;
+          a[1] = fr[1] / m;
+          a[2] = fr[2] / m;
+        } else {
 #pragma unroll
-            for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
-          }
-          done = true;
+          for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
         }
+        done = true;
       }
-      if (!done) {
-        // free node: acceleration in the element precision, checked before
-        // widening (the element force is already rounded to T)
-        const T im = D.inv_mass[j];
-        const T ax = D.grav_t[0] - fx * im, ay = D.grav_t[1] - fy * im, az = D.grav_t[2] - fz * im;
-        if (!xfinite(ax) || !xfinite(ay) || !xfinite(az)) nonfin = 1;
-        a[0] = to_f64(ax);
-        a[1] = to_f64(ay);
-        a[2] = to_f64(az);
-      } else if (!xfinite(a[0]) || !xfinite(a[1]) || !xfinite(a[2])) {
-        nonfin = 1;
-      }
-      const double dt = D.dt;
-      const double *dc = D.d[cur];
-      const double *vc = D.v[cur];
-      double *dn = D.d[nxt];
-      double *vn = D.v[nxt];
-      double dd[3];
-      const bool phi1 = (D.phi == 1.0);
-      const double pdt2 = D.phi * dt * dt;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
-        const double vi = vc[i * nn + j];
-        const double di = dc[i * nn + j];
-        const double v1 = vi + dt * ai;
-        const double d1 = phi1 ? di + dt * v1 : di + dt * vi + pdt2 * ai;
-        vn[i * nn + j] = v1;
-        dn[i * nn + j] = d1;
-        dd[i] = d1;
-      }
-      V4 u;
-      u.x = to_elem(dd[0], T(0));
-      u.y = to_elem(dd[1], T(0));
-      u.z = to_elem(dd[2], T(0));
-      u.w = T(0);
-      D.u4[nxt][j] = u;
     }
+    if (!done) {
+      // free node: acceleration in the element precision, checked before
+      // widening (the element force is already rounded to T)
+      const T im = D.inv_mass[j];
+      const T ax = D.grav_t[0] - fx * im, ay = D.grav_t[1] - fy * im, az = D.grav_t[2] - fz * im;
+      if (!xfinite(ax) || !xfinite(ay) || !xfinite(az)) nonfin = 1;
+      a[0] = to_f64(ax);
+      a[1] = to_f64(ay);
+      a[2] = to_f64(az);
+    } else if (!xfinite(a[0]) || !xfinite(a[1]) || !xfinite(a[2])) {
+      nonfin = 1;
+    }
+    const double dt = D.dt;
+    const double *dc = D.d[cur];
+    const double *vc = D.v[cur];
+    double *dn = D.d[nxt];
+    double *vn = D.v[nxt];
+    double dd[3];
+    const bool phi1 = (D.phi == 1.0);
+    const double pdt2 = D.phi * dt * dt;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
+      const double vi = vc[i * nn + j];
+      const double di = dc[i * nn + j];
+      const double v1 = vi + dt * ai;
+      const double d1 = phi1 ? di + dt * v1 : di + dt * vi + pdt2 * ai;
+      vn[i * nn + j] = v1;
+      dn[i * nn + j] = d1;
+      dd[i] = d1;
+    }
+    V4 u;
+    u.x = to_elem(dd[0], T(0));
+    u.y = to_elem(dd[1], T(0));
+    u.z = to_elem(dd[2], T(0));
+    u.w = T(0);
+    D.u4[nxt][j] = u;
   }
   if (nonfin) atomicOr(&ctl->nonfinite, 1);
+}
+
+// One node, its element forces read straight from global memory.  The
+// node's forces are contiguous (written at their CSR positions) and summed in
+// CSR order: hexes, then interfaces, ascending.
+template <typename T>
+__device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  if (j >= D.nn) return;
+  T fx = T(0), fy = T(0), fz = T(0);
+  const int r0 = D.row[j], r1 = D.row[j + 1];
+#pragma unroll 4
+  for (int r = r0; r < r1; ++r) {
+    const V4 f = D.fe[r];
+    fx += f.x;
+    fy += f.y;
+    fz += f.z;
+  }
+  gather_node(D, j, mode, fx, fy, fz);
 }
 
 }  // namespace detail

@@ -265,6 +265,35 @@ def large_fp32_plate(steps: int = 5000) -> Workload:
                              steps=steps)
 
 
+def batch_plates(n: int = 64, seed: int = 0, hex_min: int = 8000, hex_max: int = 400000,
+                 steps: int = 2000, fp64: bool = False) -> List[Workload]:
+    """Independent impact cases for a batched launch: plate sizes log-uniform
+    in [hex_min, hex_max] hex8 elements, seeded symmetric quasi-isotropic
+    layups of 8 to 24 plies (one element per ply, t_ply = 0.275 mm), the
+    in-plane spacing of the 100x150 mm plate (100/128 mm) at aspect 2:3,
+    striker R = 8 mm with mass uniform in 1-6 kg and speed uniform in 1-5 m/s,
+    damage and interfaces on.  Every plate has the same stable step (same
+    spacing and ply thickness)."""
+    rng = np.random.default_rng(seed)
+    h, t_ply = 100.0 / 128.0, 0.275
+    out = []
+    for k in range(n):
+        target = float(np.exp(rng.uniform(np.log(hex_min), np.log(hex_max))))
+        plies = 2 * int(rng.integers(4, 13))
+        inplane = max(target / plies, 256.0)
+        nx = max(16, int(round(np.sqrt(inplane * 2.0 / 3.0))))
+        ny = max(16, int(round(nx * 1.5)))
+        mass = float(rng.uniform(1.0e-3, 6.0e-3))
+        speed = float(rng.uniform(1000.0, 5000.0))
+        s_k = seed * 1000 + k
+        lay = seeded_quasi_isotropic_layup(plies, s_k)
+        plate = make_plate(nx * h, ny * h, plies * t_ply, nx, ny, lay, 1, cohesive=True)
+        mat = material_im7_like_config(t_ply=t_ply, seed=s_k)
+        name = f"batch{n}_seed{seed}_plate{k}_{nx}x{ny}x{plies}"
+        out.append(Workload(name, plate, mat, fp64, True, True, 8.0, mass, speed, 0.01, 0.5, steps))
+    return out
+
+
 def seeded_state(plate: Plate, seed: int, amp: float = 0.05, vamp: float = 200.0,
                  dimple=None, jitter: bool = True):
     """A smooth seeded displacement/velocity field (SoA [3, n_nodes], float64)

@@ -1,5 +1,5 @@
-"""The C-ABI library loads and exports every entry point that include/pdn.h
-declares, and the Python binding exposes the same names.  No GPU work: only
+"""The C-ABI library loads and exports every entry point that include/*.h
+declare, and the Python binding exposes the same names.  No GPU work: only
 symbol lookups and argument checks that return before any CUDA call."""
 import ctypes
 import os
@@ -12,9 +12,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "pdn.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pdn_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(pdn_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -44,6 +49,22 @@ def test_init_rejects_null_arguments_without_touching_the_device():
     L.pdn_destroy(None)
 
 
+def test_batch_init_rejects_bad_arguments_without_touching_the_device():
+    import paper_2301_05552_gb300 as pkg
+    L = pkg.lib()
+    h = ctypes.c_void_p()
+    assert L.pdn_batch_init(ctypes.byref(h), 0, None, None, None) == -1
+    assert b"n_plates" in L.pdn_batch_last_error(None)
+    assert L.pdn_batch_init(ctypes.byref(h), 2, None, None, None) == -1
+    assert b"required" in L.pdn_batch_last_error(None)
+    assert L.pdn_batch_init(None, 2, None, None, None) == -1
+    assert L.pdn_batch_step(None, 1) == -1
+    assert L.pdn_batch_get_info(None, None) == -1
+    assert L.pdn_batch_plate(None, 0) is None
+    assert L.pdn_batch_test_barrier_timeout(None, 1.0) == -1
+    L.pdn_batch_destroy(None)
+
+
 def test_struct_layouts_match_header_sizes():
     """ctypes mirrors of the header structs have the C sizes (all fields are
     8-byte scalars or pointers except the documented int32 members)."""
@@ -52,6 +73,7 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(pkg.Material) == 31 * 8
     assert ctypes.sizeof(pkg.Options) == 4 * 4 + 3 * 8 + 3 * 8 + 8 + 8
     assert ctypes.sizeof(pkg.Info) == 5 * 8 + 8 * 8 + 4 * 4 + 4 * 8
+    assert ctypes.sizeof(pkg.BatchInfo) == 10 * 4 + 4 * 8 + 2 * 8 + 16 * 8 + 3 * 16 * 4
 
 
 def test_plate_generator_topology():
