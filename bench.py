@@ -23,6 +23,11 @@ cpu_baseline = the FP64 oracle (oracle/) on a bounded sample of the same
 --impl reference times the oracle alone on the same workload (bounded sample)
 and prints its own line.  Multi-GPU: one process per GPU, each rank runs an
 independent replica (weak scaling, no data-path collective).
+
+--workload batch64 measures the batched persistent launch instead: 64 seeded
+plates of 8k-400k hex8 (6.2M in total) advanced together by pdn_batch_step,
+against the same plates advanced one after another by the plain pdn_step
+(speedup at identical peak contact forces).
 """
 from __future__ import annotations
 
@@ -160,9 +165,11 @@ def oracle_rate(w, seconds: float, max_steps: int, threads: int):
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    w = workload_for(args)
     cores = len(os.sched_getaffinity(0))
     budget = max(10.0, min(120.0, args.ref_seconds))
+    if args.workload == "batch64":
+        return run_reference_batch(args, cores, budget)
+    w = workload_for(args)
     # warm-up steps are part of the bounded sample's set-up
     rate, n, dt = oracle_rate(w, budget, max(1, args.steps), cores)
     line = {
@@ -173,6 +180,33 @@ def run_reference(args, ws, rank):
                    "n_nodes": w.plate.n_nodes, "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n} of the workload's explicit steps from rest, FP64 oracle, {cores} threads"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_reference_batch(args, cores, budget):
+    """The oracle on the 64-plate cases, plate after plate, within the time
+    budget (each plate gets an equal share of it)."""
+    import pdn_inputs as pi
+    cases = pi.batch_plates(n=64, seed=args.seed)
+    share = budget / len(cases)
+    upd, secs, steps = 0.0, 0.0, 0
+    for w in cases:
+        rate, n, dt = oracle_rate(w, share, max(1, args.steps), cores)
+        upd += w.plate.n_hex * n
+        secs += dt
+        steps += n
+    rate = upd / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch64_seed{args.seed}_8k-400k_hex8", "n_plates": len(cases),
+                   "n_hex": sum(w.plate.n_hex for w in cases), "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} explicit steps over the 64 plates ({secs:.1f} s), FP64 oracle"},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -298,10 +332,114 @@ def run_gpu(args, ws, rank, local):
     return 0
 
 
+def run_batch(args, ws, rank, local):
+    """64 independent plates: pdn_batch_step against pdn_step plate after
+    plate, same steps, same stream."""
+    import numpy as np
+    import torch
+
+    import paper_2301_05552_gb300 as pkg
+    import pdn_inputs as pi
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.lib()
+    cases = pi.batch_plates(n=64, seed=args.seed)
+    K, W = args.steps, args.warmup
+    n_hex = sum(w.plate.n_hex for w in cases)
+    stream = torch.cuda.Stream()
+    prec = pkg.PDN_FP32_FORCE
+    b = pkg.pdn_batch_init([w.plate for w in cases], [w.material for w in cases], precision=prec,
+                           damage_on=True, plasticity_on=True, stream=stream.cuda_stream)
+    for c, w in zip(b.plates, cases):
+        pkg.pdn_set_impactor(c, *w.impactor())
+    pkg.pdn_batch_step(b, W)  # the first call also runs the schedule autotuner
+    info0 = pkg.pdn_batch_get_info(b)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        pkg.pdn_batch_step(b, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_batch = ev0.elapsed_time(ev1)
+    info = pkg.pdn_batch_get_info(b)
+    peaks_b = np.array([pkg.pdn_contact_force(c)[1] for c in b.plates])
+    repeats_b = sum(pkg.pdn_get_info(c)["n_repeats"] for c in b.plates)
+    b.close()
+
+    # the plain step: one context per plate, stepped one after another
+    ctxs = []
+    for w in cases:
+        c = pkg.pdn_init_mesh(w.plate, w.material, precision=prec, damage_on=True, plasticity_on=True,
+                              stream=stream.cuda_stream)
+        pkg.pdn_set_impactor(c, *w.impactor())
+        pkg.pdn_step(c, W)
+        ctxs.append(c)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for c in ctxs:
+        pkg.pdn_step(c, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = ev0.elapsed_time(ev1)
+    peaks_p = np.array([pkg.pdn_contact_force(c)[1] for c in ctxs])
+    for c in ctxs:
+        c.close()
+    if dist is not None:
+        t = torch.tensor([ms_batch, ms_plain], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_batch, ms_plain = (float(x) for x in t.tolist())
+    value = ws * n_hex * K / (ms_batch * 1e-3)
+    alg = sum(step_alg_bytes(w.plate.n_hex, w.plate.n_coh, w.plate.n_nodes, w.plate.n_surf) for w in cases)
+    peak_gbs, peak_kind = measured_peaks()
+    achieved = alg * K / (ms_batch * 1e-3) / 1e9
+    scale = np.maximum(np.abs(peaks_p), 1e-300)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms_batch / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": f"batch64_seed{args.seed}_8k-400k_hex8", "n_plates": len(cases), "n_hex": n_hex,
+            "n_coh": sum(w.plate.n_coh for w in cases), "n_nodes": sum(w.plate.n_nodes for w in cases),
+            "hex_per_plate_min_max": [min(w.plate.n_hex for w in cases), max(w.plate.n_hex for w in cases)],
+            "precision": "FP32 element forces/damage/cohesive, FP64 integration, striker and gap test",
+            "l2": "inputs larger than L2", "step_alg_bytes": alg, "parallelism": f"replicas x{ws}",
+        },
+        "batch": {
+            "speedup_vs_plain_step": ms_plain / ms_batch,
+            "plain_value": ws * n_hex * K / (ms_plain * 1e-3), "plain_ms_per_step": ms_plain / K,
+            "f_peak_max_rel_diff_vs_plain": float(np.max(np.abs(peaks_b - peaks_p) / scale)),
+            "f_peak_N_range": [float(peaks_b.min()), float(peaks_b.max())],
+            "step_repeats": int(repeats_b),
+            "schedule": {k: info[k] for k in ("blocks_per_sm", "tile_items", "reg_variant", "grid", "graph")},
+            "autotune_candidates": info0["candidates"],
+            "passes": info["passes"] - info0["passes"], "launches": info["launches"] - info0["launches"],
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "traffic": None, "kernel": "k_batch (whole step)",
+                     "alg_bytes_per_step": alg, "peak_kind": peak_kind},
+        "gpu_launches": int(info["launches"] - info0["launches"]),
+        "clocks": clocks.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in ("pdn_kernels.cu", "pdn_internal.h"):
+    for name in ("pdn_kernels.cu", "pdn_items.cuh", "pdn_device.cuh", "pdn_internal.h"):
         with open(os.path.join(ROOT, "paper_2301_05552_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -310,7 +448,8 @@ def kernel_source_hash() -> str:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 20000 for the plate, 500 for batch64)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--seed", type=int, default=0)
@@ -318,12 +457,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["plate", "batch64"], default="plate")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 500 if args.workload == "batch64" else 20000
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "batch64":
+        return run_batch(args, ws, rank, local)
     return run_gpu(args, ws, rank, local)
 
 
