@@ -160,7 +160,9 @@ typedef struct {
   int32_t status;          /* sticky device status (PDN_OK or an error code) */
   int32_t precision;
   int32_t hex_variant;     /* hex-kernel launch variant chosen by the autotuner
-                              (occupancy target 4, 5, 6 or 3 blocks/SM for 0..3) */
+                              (occupancy target 4, 5, 6 or 3 blocks/SM for 0..3);
+                              the environment variable PDN_HEX_VARIANT=0..3 fixes
+                              it instead (no timing, tune_ms stays 0) */
   int32_t reserved;
   double tune_ms[4];       /* mean hex-kernel time of each variant when tuned (0 if not) */
 } pdn_info;

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -594,7 +595,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     chk(cudaMemset(d_v[b], 0, sizeof(double) * 3 * nn));
     chk(cudaMemset(d_u4[b], 0, ts * 4 * nn));
     chk(cudaMemset(d_rD[b], 0, ts * 4 * std::max<int64_t>(nc, 1)));
-    chk(cudaMemset(d_act[b], 0, std::max<int64_t>(ns, 1)));
+    chk(cudaMemset(d_act[b], 0, (std::max<int64_t>(ns, 1) + 15) & ~int64_t(15)));  // padding included
     chk(cudaMemset(P.pflag[b], 1, nh));  // every element starts with the initial history
     chk(cudaMemset(P.cflag[b], 1, std::max<int64_t>(nc, 1)));
     if (fp64)
@@ -715,6 +716,13 @@ int autotune(pdn_ctx *ctx) {
   ctx->tuned = true;
   const int nvar = ctx->precision == PDN_FP64 ? 1 : 4;
   if (nvar == 1) return PDN_OK;
+  // a fixed variant instead of timing (reproducible profiling runs)
+  if (const char *fv = std::getenv("PDN_HEX_VARIANT")) {
+    if (fv[0] >= '0' && fv[0] < '0' + nvar && fv[1] == '\0') {
+      ctx->Df.hex_variant = fv[0] - '0';
+      return PDN_OK;
+    }
+  }
   cudaEvent_t ev[6];
   for (int k = 0; k < 6; ++k) PDN_CU(cudaEventCreate(&ev[k]), "tune event");
   int best = 0;

@@ -673,49 +673,117 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
       ss = *D.imp_step;
     }
   }
-  // The surface is cut into kTailLanes contiguous ranges of 16-flag words,
-  // reduced in a fixed tree: xor-shuffles within each group of 32 ranges,
-  // then the groups in order.  A block of any size that divides kTailLanes
-  // (>= 32) plays the ranges as virtual threads, so the sum and its rounding
-  // do not depend on the launch shape.
+  // Reaction sum over the active contact nodes in a fixed order that does
+  // not depend on the launch shape: the active nodes are listed in surface
+  // order (flags counted per range of 16-flag words, ranges prefix-summed,
+  // indices written in order); list entry i goes to virtual lane i mod
+  // kTailLanes, each lane sums its entries in list order, lanes are reduced
+  // by xor-shuffles within groups of 32 and the groups in order.  A block of
+  // any size that divides kTailLanes (>= 32) plays the lanes in turn.  The
+  // list lets every thread issue its loads of lambda and n together; when
+  // more than kTailCap nodes are active, each lane instead sums the active
+  // nodes of its own word range in order.
   constexpr int kTailLanes = 256;
+  constexpr int kTailCap = 4096;
   __shared__ double tf[3][kTailLanes / 32];
   __shared__ int ti[2][kTailLanes / 32];
+  __shared__ int s_off[kTailLanes];
+  __shared__ int s_list[kTailCap];
   const int64_t ns = D.ns;
   const int64_t words = (ns + 15) / 16;
   const int64_t per = (words + kTailLanes - 1) / kTailLanes;
+  // the flag arrays are 256-byte aligned, sized to a multiple of 16 bytes,
+  // and hold 0 or 1 per node
   const uint4 *aw = stepping ? reinterpret_cast<const uint4 *>(D.act[(int)((ctl->step + 1) & 1)]) : nullptr;
-  for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
-    const int v = v0 + (int)threadIdx.x;  // virtual thread
-    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-    int nact = 0, nadh = 0;
-    if (stepping) {
-      // the flag arrays are 256-byte aligned and sized to a multiple of 16
-      // bytes; the words are loaded together and only the rare set flags
-      // lead to further loads
+  int total = 0;
+  if (stepping) {
+    for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
+      const int v = v0 + (int)threadIdx.x;
       const int64_t w0 = (int64_t)v * per;
       const int64_t w1 = w0 + per < words ? w0 + per : words;
-      for (int64_t wi = w0; wi < w1; wi += 4) {
-        uint4 q[4];
+      int cnt = 0;
+      for (int64_t wi = w0; wi < w1; ++wi) {
+        const uint4 q = aw[wi];
+        cnt += __popc(q.x & 0x01010101u) + __popc(q.y & 0x01010101u) + __popc(q.z & 0x01010101u) +
+               __popc(q.w & 0x01010101u);
+      }
+      s_off[v] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive prefix over the lanes, 8 per thread
+      const int l = threadIdx.x;
+      int loc[kTailLanes / 32], acc = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = (wi + u < w1) ? aw[wi + u] : make_uint4(0u, 0u, 0u, 0u);
+      for (int k = 0; k < kTailLanes / 32; ++k) {
+        loc[k] = acc;
+        acc += s_off[l * (kTailLanes / 32) + k];
+      }
+      int inc = acc;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if ((q[u].x | q[u].y | q[u].z | q[u].w) == 0u) continue;
-          const uint32_t part[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
-          for (int b = 0; b < 16; ++b) {
-            if (!((part[b >> 2] >> (8 * (b & 3))) & 0xffu)) continue;
-            const int64_t s = (wi + u) * 16 + b;
-            if (s >= ns) continue;
-            const double lam = D.lam[s];
-            if (lam < 0.0) {
-              ++nadh;
-            } else {
-              ++nact;
-              f0 += lam * D.nrm[s];
-              f1 += lam * D.nrm[ns + s];
-              f2 += lam * D.nrm[2 * ns + s];
-            }
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += t;
+      }
+      const int base = inc - acc;
+#pragma unroll
+      for (int k = 0; k < kTailLanes / 32; ++k) s_off[l * (kTailLanes / 32) + k] = base + loc[k];
+      if (l == 31) s_list[0] = inc;  // total, read below before the list is written
+    }
+    __syncthreads();
+    total = s_list[0];
+    __syncthreads();
+    if (total <= kTailCap) {
+      for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
+        const int v = v0 + (int)threadIdx.x;
+        const int64_t w0 = (int64_t)v * per;
+        const int64_t w1 = w0 + per < words ? w0 + per : words;
+        int o = s_off[v];
+        for (int64_t wi = w0; wi < w1; ++wi) {
+          const uint4 q = aw[wi];
+          if ((q.x | q.y | q.z | q.w) == 0u) continue;
+          const uint32_t part[4] = {q.x, q.y, q.z, q.w};
+          for (int b = 0; b < 16; ++b)
+            if ((part[b >> 2] >> (8 * (b & 3))) & 1u) s_list[o++] = (int)(wi * 16 + b);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
+    const int v = v0 + (int)threadIdx.x;  // virtual lane
+    double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    int nact = 0, nadh = 0;
+    if (stepping && total <= kTailCap) {
+      for (int i = v; i < total; i += kTailLanes) {
+        const int64_t s = s_list[i];
+        const double lam = D.lam[s];
+        if (lam < 0.0) {
+          ++nadh;
+        } else {
+          ++nact;
+          f0 += lam * D.nrm[s];
+          f1 += lam * D.nrm[ns + s];
+          f2 += lam * D.nrm[2 * ns + s];
+        }
+      }
+    } else if (stepping) {
+      const int64_t w0 = (int64_t)v * per;
+      const int64_t w1 = w0 + per < words ? w0 + per : words;
+      for (int64_t wi = w0; wi < w1; ++wi) {
+        const uint4 q = aw[wi];
+        if ((q.x | q.y | q.z | q.w) == 0u) continue;
+        const uint32_t part[4] = {q.x, q.y, q.z, q.w};
+        for (int b = 0; b < 16; ++b) {
+          if (!((part[b >> 2] >> (8 * (b & 3))) & 1u)) continue;
+          const int64_t s = wi * 16 + b;
+          const double lam = D.lam[s];
+          if (lam < 0.0) {
+            ++nadh;
+          } else {
+            ++nact;
+            f0 += lam * D.nrm[s];
+            f1 += lam * D.nrm[ns + s];
+            f2 += lam * D.nrm[2 * ns + s];
           }
         }
       }
