@@ -28,6 +28,11 @@ independent replica (weak scaling, no data-path collective).
 plates of 8k-400k hex8 (6.2M in total) advanced together by pdn_batch_step,
 against the same plates advanced one after another by the plain pdn_step
 (speedup at identical peak contact forces).
+
+--workload surrogate trains the learned intralaminar law (generation and
+training times reported), measures its held-out accuracy, and runs the
+100x150 mm plate with the learned law against the exact law (step time and
+peak contact force).
 """
 from __future__ import annotations
 
@@ -436,6 +441,109 @@ def run_batch(args, ws, rank, local):
     return 0
 
 
+def run_surrogate(args, ws, rank, local):
+    """The learned law on the 128x192x16 plate against the exact law."""
+    import numpy as np
+    import torch
+
+    import paper_2301_05552_gb300 as pkg
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pkg.lib()
+    w = workload_for(args)
+    plate = w.plate
+    K, W = args.steps, args.warmup
+    Lx, Ly, H = plate.dims
+    nx, ny = plate.grid[:2]
+    plies = len(plate.ply_angle_deg)
+    lc = (Lx / nx * Ly / ny * H / plies) ** (1.0 / 3.0)
+    stream = torch.cuda.Stream()
+    s = pkg.pdn_sur_create(w.material, lc, seed=args.seed + 1, stream=stream.cuda_stream)
+    n_paths, steps_pp, iters, batch = 1_000_000, 8, 40000, 8192
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_kept = pkg.pdn_sur_generate(s, n_paths, steps_pp, 0.01, 0.4, 0.9, seed=args.seed + 11)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = pkg.pdn_sur_train(s, iters, batch, 2e-3, seed=args.seed + 3)
+    t_train = time.perf_counter() - t0
+    h = pkg.pdn_sur_create(w.material, lc, seed=0, stream=stream.cuda_stream)
+    n_hold = pkg.pdn_sur_generate(h, 20000, steps_pp, 0.01, 0.4, 0.9, seed=args.seed + 99)
+    xh, yh = pkg.pdn_sur_get_data(h, 0, n_hold)
+    h.close()
+    yp = pkg.pdn_sur_forward(s, xh)
+    rms = np.sqrt(np.mean(yh[:, :6].astype(np.float64) ** 2, axis=0))
+    rel_rms = np.sqrt(np.mean((yp[:, :6] - yh[:, :6]).astype(np.float64) ** 2, axis=0)) / rms
+    rel_max = np.max(np.abs(yp[:, :6] - yh[:, :6]), axis=0) / rms
+    r_err = float(np.max(np.abs(yp[:, 6:] - yh[:, 6:])))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = {}
+    clock_summary = None
+    for mode in ("exact", "learned"):
+        with torch.cuda.stream(stream):
+            g = pkg.Solver(w, stream=stream.cuda_stream)
+        if mode == "learned":
+            pkg.pdn_set_surrogate(g.ctx, s, 0.9)
+        pkg.pdn_step(g.ctx, W)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clocks:
+            ev0.record(stream)
+            pkg.pdn_step(g.ctx, K)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if mode == "learned":
+            clock_summary = clocks.summary()
+        ms = ev0.elapsed_time(ev1)
+        prof = pkg.pdn_profile_kernels(g.ctx, args.profile_steps)
+        fh = pkg.pdn_contact_force(g.ctx)[2]
+        runs[mode] = dict(ms=ms, hex_ms=prof["hex"][0], f_peak=float(fh.max()) if len(fh) else 0.0,
+                          kernel_ms={k: v[0] for k, v in prof.items()})
+        g.close()
+    s.close()
+    ex, le = runs["exact"], runs["learned"]
+    # tensor-core work of the learned-law hex kernel: every Gauss point of
+    # every warp that needs the network runs it (padded 16-wide input and
+    # output layers): 2 * (16*64 + 2*64*64 + 64*16) flops per point
+    flops = plate.n_hex * 8 * 2 * (16 * 64 + 2 * 64 * 64 + 64 * 16)
+    peak_tf = 1900.8
+    try:
+        peak_tf = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    ach = flops / (le["hex_ms"] * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": plate.n_hex * K / (le["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": le["ms"] / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (network) + f32 + f64", "data": "synthetic",
+        "config": {"workload": w.name + "_learned_law", "n_hex": plate.n_hex, "n_coh": plate.n_coh,
+                   "n_nodes": plate.n_nodes, "l2": "inputs larger than L2", "onset_ratio": 0.9,
+                   "network": "10-64-64-64-10 ReLU, BF16 weights, FP32 accumulation (mma.sync m16n8k16)"},
+        "surrogate": {
+            "speedup_vs_exact_law": ex["ms"] / le["ms"], "exact_ms_per_step": ex["ms"] / K,
+            "exact_value": plate.n_hex * K / (ex["ms"] * 1e-3),
+            "f_peak_N_exact": ex["f_peak"], "f_peak_N_learned": le["f_peak"],
+            "f_peak_rel_diff": abs(le["f_peak"] - ex["f_peak"]) / max(ex["f_peak"], 1e-300),
+            "hex_ms_exact": ex["hex_ms"], "hex_ms_learned": le["hex_ms"],
+            "kernel_ms_learned": le["kernel_ms"],
+            "held_out_points": n_hold, "held_out_rel_rms_stress_err": [float(v) for v in rel_rms],
+            "held_out_rel_max_stress_err": [float(v) for v in rel_max], "held_out_max_abs_threshold_err": r_err,
+            "train": {"paths": n_paths, "steps_per_path": steps_pp, "points_kept": n_kept, "iters": iters,
+                      "batch": batch, "seconds": t_train, "generate_seconds": t_gen,
+                      "loss_first": float(loss[0]), "loss_last": float(loss[-1])},
+        },
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s", "frac": ach / peak_tf,
+                     "traffic": None, "kernel": "k_hex_sur (learned law)", "flops_per_launch": flops,
+                     "launch_ms": le["hex_ms"], "peak_kind": "measured bf16 (dense GEMM, burst)"},
+        "gpu_launches": None,
+        "clocks": clock_summary,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -457,7 +565,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["plate", "batch64"], default="plate")
+    ap.add_argument("--workload", choices=["plate", "batch64", "surrogate"], default="plate")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 500 if args.workload == "batch64" else 20000
@@ -468,6 +576,8 @@ def main():
         return run_reference(args, ws, rank)
     if args.workload == "batch64":
         return run_batch(args, ws, rank, local)
+    if args.workload == "surrogate":
+        return run_surrogate(args, ws, rank, local)
     return run_gpu(args, ws, rank, local)
 
 

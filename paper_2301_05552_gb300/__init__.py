@@ -28,6 +28,9 @@ __all__ = [
     "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
     "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
     "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
+    "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
+    "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate",
+    "pdn_sur_destroy", "pdn_sur_last_error", "pdn_sur_get_data", "SUR_PARAMS", "SUR_SCALING",
     "PDN_FP64", "PDN_FP32_FORCE", "FIELDS", "KERNELS",
 ]
 
@@ -41,7 +44,12 @@ EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force",
            "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
            "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
            "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
-           "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error"]
+           "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
+           "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
+           "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate",
+           "pdn_sur_destroy", "pdn_sur_last_error", "pdn_sur_get_data"]
+SUR_PARAMS = 9674
+SUR_SCALING = 60
 
 
 class PdnError(RuntimeError):
@@ -142,6 +150,26 @@ def lib():
             L.pdn_batch_last_error.argtypes = [vp]
             L.pdn_batch_last_error.restype = C.c_char_p
             for name in ("pdn_batch_init", "pdn_batch_step", "pdn_batch_get_info", "pdn_batch_test_barrier_timeout"):
+                getattr(L, name).restype = C.c_int
+            fp = C.POINTER(C.c_float)
+            L.pdn_sur_create.argtypes = [C.POINTER(vp), C.POINTER(Material), C.c_double, C.c_uint64, vp]
+            L.pdn_sur_generate.argtypes = [vp, C.c_int64, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                           C.c_uint64, C.POINTER(C.c_int64)]
+            L.pdn_sur_train.argtypes = [vp, C.c_int64, C.c_int32, C.c_double, C.c_uint64, dp]
+            L.pdn_sur_get_data.argtypes = [vp, C.c_int64, C.c_int64, fp, fp]
+            L.pdn_sur_get_data.restype = C.c_int
+            L.pdn_sur_forward.argtypes = [vp, vp, vp, C.c_int64, C.c_int32]
+            L.pdn_sur_exact.argtypes = [vp, vp, vp, C.c_int64, C.c_int32]
+            L.pdn_sur_gradient.argtypes = [vp, fp, fp, C.c_int64, fp, dp]
+            L.pdn_sur_get_params.argtypes = [vp, fp, fp]
+            L.pdn_sur_set_params.argtypes = [vp, fp, fp]
+            L.pdn_set_surrogate.argtypes = [vp, vp, C.c_double]
+            L.pdn_sur_destroy.argtypes = [vp]
+            L.pdn_sur_destroy.restype = None
+            L.pdn_sur_last_error.argtypes = [vp]
+            L.pdn_sur_last_error.restype = C.c_char_p
+            for name in ("pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
+                         "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate"):
                 getattr(L, name).restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
                          "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
@@ -468,6 +496,116 @@ def pdn_batch_destroy(b: Batch):
 
 def pdn_batch_last_error(b: Optional[Batch]) -> str:
     return (lib().pdn_batch_last_error(b.handle if b is not None else None) or b"").decode()
+
+
+class Surrogate:
+    """A pdn_surrogate handle (learned intralaminar law)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().pdn_sur_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _scheck(s, rc):
+    if rc < 0:
+        msg = lib().pdn_sur_last_error(s.handle if s is not None else None)
+        raise PdnError(int(rc), (msg or b"").decode())
+    return rc
+
+
+def pdn_sur_create(material: dict, lc: float, seed: int = 0, stream: Optional[int] = None) -> Surrogate:
+    L = lib()
+    h = C.c_void_p()
+    if stream is None:
+        stream = _current_stream()
+    rc = L.pdn_sur_create(C.byref(h), C.byref(_material(material)), float(lc), int(seed), stream)
+    if rc < 0:
+        raise PdnError(rc, (L.pdn_sur_last_error(None) or b"").decode())
+    return Surrogate(h)
+
+
+def pdn_sur_generate(s: Surrogate, n_paths: int, steps_per_path: int = 8, strain_max: float = 0.01,
+                     cyclic_fraction: float = 0.4, onset_ratio: float = 0.9, seed: int = 0) -> int:
+    n = C.c_int64()
+    _scheck(s, lib().pdn_sur_generate(s.handle, int(n_paths), int(steps_per_path), float(strain_max),
+                                      float(cyclic_fraction), float(onset_ratio), int(seed), C.byref(n)))
+    return int(n.value)
+
+
+def pdn_sur_get_data(s: Surrogate, offset: int, n: int):
+    """Points [offset, offset+n) of the training set: (x[n,10], y[n,10]) raw."""
+    x = np.zeros((int(n), 10), dtype=np.float32)
+    y = np.zeros((int(n), 10), dtype=np.float32)
+    _scheck(s, lib().pdn_sur_get_data(s.handle, int(offset), int(n), _ptr(x, C.c_float), _ptr(y, C.c_float)))
+    return x, y
+
+
+def pdn_sur_train(s: Surrogate, iters: int, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
+    loss = np.zeros(max(int(iters), 1))
+    _scheck(s, lib().pdn_sur_train(s.handle, int(iters), int(batch), float(lr), int(seed), _ptr(loss, C.c_double)))
+    return loss[: int(iters)]
+
+
+def _points(s, fn, x):
+    x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 10)
+    y = np.zeros_like(x)
+    _scheck(s, fn(s.handle, x.ctypes.data_as(C.c_void_p), y.ctypes.data_as(C.c_void_p), x.shape[0], 0))
+    return y
+
+
+def pdn_sur_forward(s: Surrogate, x):
+    """Network output for raw points x[n, 10] (strain 6, thresholds 4)."""
+    return _points(s, lib().pdn_sur_forward, x)
+
+
+def pdn_sur_exact(s: Surrogate, x):
+    """Exact damage law (FP64 on the GPU) for the same points."""
+    return _points(s, lib().pdn_sur_exact, x)
+
+
+def pdn_sur_gradient(s: Surrogate, xn, tn):
+    xn = np.ascontiguousarray(xn, dtype=np.float32).reshape(-1, 10)
+    tn = np.ascontiguousarray(tn, dtype=np.float32).reshape(-1, 10)
+    g = np.zeros(SUR_PARAMS, dtype=np.float32)
+    loss = np.zeros(1)
+    _scheck(s, lib().pdn_sur_gradient(s.handle, _ptr(xn, C.c_float), _ptr(tn, C.c_float), xn.shape[0],
+                                      _ptr(g, C.c_float), _ptr(loss, C.c_double)))
+    return g, float(loss[0])
+
+
+def pdn_sur_get_params(s: Surrogate):
+    p = np.zeros(SUR_PARAMS, dtype=np.float32)
+    sc = np.zeros(SUR_SCALING, dtype=np.float32)
+    _scheck(s, lib().pdn_sur_get_params(s.handle, _ptr(p, C.c_float), _ptr(sc, C.c_float)))
+    return p, sc
+
+
+def pdn_sur_set_params(s: Surrogate, params=None, scaling=None):
+    p = None if params is None else np.ascontiguousarray(params, dtype=np.float32)
+    sc = None if scaling is None else np.ascontiguousarray(scaling, dtype=np.float32)
+    _scheck(s, lib().pdn_sur_set_params(s.handle, _ptr(p, C.c_float), _ptr(sc, C.c_float)))
+
+
+def pdn_set_surrogate(ctx: Context, s: Optional[Surrogate], onset_ratio: float = 0.9):
+    _check(ctx, lib().pdn_set_surrogate(ctx.handle, s.handle if s is not None else None, float(onset_ratio)))
+
+
+def pdn_sur_destroy(s: Surrogate):
+    s.close()
+
+
+def pdn_sur_last_error(s: Optional[Surrogate]) -> str:
+    return (lib().pdn_sur_last_error(s.handle if s is not None else None) or b"").decode()
 
 
 class Solver:

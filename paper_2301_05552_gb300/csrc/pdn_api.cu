@@ -262,6 +262,7 @@ void pdn_destroy(pdn_ctx *ctx) {
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->arena.base) cudaFree(ctx->arena.base);
+  if (ctx->sur_buf) cudaFree(ctx->sur_buf);
   if (ctx->ctl_host) cudaFreeHost(ctx->ctl_host);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->side) cudaStreamDestroy(ctx->side);

@@ -56,6 +56,7 @@ struct pdn_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<cudaEvent_t> prof_ev;
+  float *sur_buf = nullptr;  // learned-law parameters and scaling (pdn_set_surrogate)
   std::string err;
 
   // Pointers common to both precisions.

@@ -153,7 +153,7 @@ __device__ T hex_volume(const T (&am)[8][3]) {
 }
 
 // SplitMix64 finaliser of (seed ^ (4 e + k)) mapped to [1 - spread, 1 + spread].
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ULL;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
@@ -216,24 +216,83 @@ __device__ __forceinline__ ElemLaw<T> elem_law(const Mat<T> &M, int64_t e) {
 // only when a threshold grows; likewise the yield test of the plasticity.
 // vol is the element volume when known up front (boxes), else am is used to
 // compute it lazily.
+// Shear plasticity of Algorithm 4 (radial return on the 12/13 pair), in
+// place on the history h[4..6].
+template <typename T>
+__device__ __forceinline__ void cdm_plastic(const Mat<T> &M, const T (&ep)[6], T (&h)[7]) {
+  if (!M.plasticity_on) return;
+  T gp12 = h[4], gp13 = h[5], pb = h[6];
+  const T t12 = M.G12 * (ep[3] - gp12);
+  const T t13 = M.G12 * (ep[4] - gp13);
+  const T tn2 = t12 * t12 + t13 * t13;
+  const T ty = M.Sp + M.KpG12 * pb;
+  if (tn2 > ty * ty) {
+    const T tn = xsqrt(tn2);
+    const T dp = (tn - ty) * M.iG1Kp;
+    const T f = dp / tn;
+    gp12 += f * t12;
+    gp13 += f * t13;
+    pb += dp;
+  }
+  h[4] = gp12;
+  h[5] = gp13;
+  h[6] = pb;
+}
+
+// Largest squared ratio phi_N^2 / r_N^2 over the four mechanisms of the
+// intralaminar law at elastic strain ee (the loading functions of cdm_damage,
+// evaluated without updating anything): > 1 means a threshold would grow.
+template <typename T>
+__device__ __forceinline__ T cdm_onset_ratio2(const Mat<T> &M, const ElemLaw<T> &L, const T (&ee)[6],
+                                              const T (&h)[7]) {
+  const T e0 = ee[0], e1 = ee[1], e2 = ee[2];
+  const T s11 = M.C11 * e0 + M.C12 * e1 + M.C13 * e2;
+  const T s22 = M.C12 * e0 + M.C22 * e1 + M.C23 * e2;
+  const T s12 = M.G12 * ee[3], s13 = M.G13 * ee[4], s23 = M.G23 * ee[5];
+  const T phiFT = M.E1 * e0 * L.iXT;
+  const T phiFC = (s11 < T(0) ? -s11 : T(0)) * M.iXC;
+  const T tl2 = s12 * s12 + s13 * s13;
+  T rat = phiFT * phiFT / (h[0] * h[0]);
+  const T rc = phiFC * phiFC / (h[1] * h[1]);
+  rat = rc > rat ? rc : rat;
+  if (s22 >= T(0)) {
+    const T a = s22 * L.iYT;
+    const T q = M.g1 * a + M.g * a * a + tl2 * L.iSL2 + s23 * s23 * M.iST2;
+    const T rm = q / (h[2] * h[2]);
+    rat = rm > rat ? rm : rat;
+  } else {
+    T tT = -s22 * M.kT;
+    tT = tT > T(0) ? tT : T(0);
+    T tL = xsqrt(tl2) + L.etaL * s22;
+    tL = tL > T(0) ? tL : T(0);
+    const T q = (tT * tT + s23 * s23) * M.iST2 + tL * tL * L.iSL2;
+    const T rm = q / (h[3] * h[3]);
+    rat = rm > rat ? rm : rat;
+  }
+  return rat;
+}
+
+// Intralaminar law (Algorithm 4) at one point: the plasticity of
+// cdm_plastic, then the damage part (cdm_damage) on the elastic strain.
+template <typename T>
+__device__ __forceinline__ void cdm_damage(const Mat<T> &M, const ElemLaw<T> &L, const T (*am)[3], T vol, T &lc,
+                                           const T (&ep)[6], T (&h)[7], T (&s)[6]);
+
 template <typename T>
 __device__ __forceinline__ void cdm(const Mat<T> &M, const ElemLaw<T> &L, const T (*am)[3], T vol, T &lc,
                                     const T (&ep)[6], T (&h)[7], T (&s)[6]) {
-  T rFT = h[0], rFC = h[1], rMT = h[2], rMC = h[3], gp12 = h[4], gp13 = h[5], pb = h[6];
-  if (M.plasticity_on) {
-    const T t12 = M.G12 * (ep[3] - gp12);
-    const T t13 = M.G12 * (ep[4] - gp13);
-    const T tn2 = t12 * t12 + t13 * t13;
-    const T ty = M.Sp + M.KpG12 * pb;
-    if (tn2 > ty * ty) {
-      const T tn = xsqrt(tn2);
-      const T dp = (tn - ty) * M.iG1Kp;
-      const T f = dp / tn;
-      gp12 += f * t12;
-      gp13 += f * t13;
-      pb += dp;
-    }
-  }
+  cdm_plastic(M, ep, h);
+  cdm_damage(M, L, am, vol, lc, ep, h, s);
+}
+
+// Damage part of Algorithm 4: loading functions on the effective stress of
+// the elastic strain (ep minus the plastic shear strains h[4], h[5]),
+// thresholds, damage variables and the nominal stress.
+template <typename T>
+__device__ __forceinline__ void cdm_damage(const Mat<T> &M, const ElemLaw<T> &L, const T (*am)[3], T vol, T &lc,
+                                           const T (&ep)[6], T (&h)[7], T (&s)[6]) {
+  T rFT = h[0], rFC = h[1], rMT = h[2], rMC = h[3];
+  const T gp12 = h[4], gp13 = h[5];
   const T e0 = ep[0], e1 = ep[1], e2 = ep[2], e3 = ep[3] - gp12, e4 = ep[4] - gp13, e5 = ep[5];
   const T s11 = M.C11 * e0 + M.C12 * e1 + M.C13 * e2;
   const T s22 = M.C12 * e0 + M.C22 * e1 + M.C23 * e2;
@@ -300,9 +359,6 @@ __device__ __forceinline__ void cdm(const Mat<T> &M, const ElemLaw<T> &L, const 
   h[1] = rFC;
   h[2] = rMT;
   h[3] = rMC;
-  h[4] = gp12;
-  h[5] = gp13;
-  h[6] = pb;
 }
 
 // ---------------------------------------------------------------------------

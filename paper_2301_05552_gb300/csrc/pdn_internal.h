@@ -147,6 +147,13 @@ struct Dev {
   // (0: 4 blocks of 128 per SM, 1: 5, 2: 6, 3: 3).  The variants execute the
   // same arithmetic, so the choice does not change any result.
   int32_t hex_variant;
+  // learned law (FP32 box elements only): the network's parameters followed
+  // by its scaling (include/pdn_surrogate.h), or nullptr for the exact law;
+  // points whose squared loading-function ratio exceeds sur_ratio2 (or whose
+  // inputs leave the training box) take the exact law
+  const float *sur_params;
+  float sur_ratio2;
+  int32_t sur_pad;
 };
 
 // Launchers (pdn_kernels.cu).
@@ -155,6 +162,8 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
                         cudaEvent_t *ev /* [6] or nullptr */, cudaStream_t side = nullptr,
                         cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 cudaError_t launch_striker_init(Striker *S, StrikerStep *ss, double dt, cudaStream_t s);
+// Hex kernel with the learned law (pdn_surrogate.cu); D.sur_params != nullptr.
+cudaError_t launch_hex_sur(const Dev<float> &D, const Mat<float> &M, cudaStream_t s);
 template <typename T>
 cudaError_t launch_damage_field(const Dev<T> &D, const Mat<T> &M, int which, float *out,
                                 cudaStream_t s);

@@ -13,6 +13,7 @@
 #include "pdn_internal.h"
 
 #include <cstdint>
+#include <type_traits>
 
 #include "pdn.h"
 #include "pdn_device.cuh"
@@ -155,6 +156,12 @@ inline int grid_of(int64_t n, int b) {
 // registers per thread) chosen per context by the autotuner.
 template <typename T>
 void launch_hex(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (D.sur_params != nullptr && D.all_boxes) {
+      launch_hex_sur(D, M, s);
+      return;
+    }
+  }
   const int g = grid_of(D.nh, 128);
   if (D.all_boxes) {
     switch (D.hex_variant) {

@@ -1,0 +1,1097 @@
+// Learned surrogate of the intralaminar damage law (include/pdn_surrogate.h):
+// training data from the exact law on the GPU, training (forward, backward,
+// weight gradients, Adam) and inference with BF16 tensor-core kernels
+// (mma.sync m16n8k16, FP32 accumulation), and the hook that lets the hex
+// kernel use it.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pdn.h"
+#include "pdn_context.h"
+#include "pdn_device.cuh"
+#include "pdn_internal.h"
+#include "pdn_mlp.cuh"
+#include "pdn_surrogate.h"
+
+namespace pdn {
+template <typename T>
+int fill_mat_public(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_plies, int damage_on,
+                    int plasticity_on, std::string &why);
+
+namespace {
+
+using namespace detail;
+using namespace mlp;
+
+constexpr int kWarps = 4;                 // warps per block of the tile kernels
+constexpr int kChunk = 128;               // points per weight-gradient partial
+constexpr int kLayers = 4;
+// padded output and input widths of layer l (0..3)
+__host__ __device__ constexpr int layer_out(int l) { return l == 3 ? kOutPad : kHid; }
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kInPad : kHid; }
+
+// ---------------------------------------------------------------------------
+// Exact damage law on elastic strains (the plastic part of Algorithm 4 is
+// not an input of the surrogate).
+
+struct LawArgs {
+  Mat<double> M;
+  ElemLaw<double> L;
+  double lc;
+};
+
+__device__ __forceinline__ void law_point(const LawArgs &A, const double (&ee)[6], double (&h)[7], double (&s)[6]) {
+  double lc = A.lc;
+  cdm_damage(A.M, A.L, (const double(*)[3]) nullptr, 0.0, lc, ee, h, s);
+}
+
+__device__ __forceinline__ double u01(uint64_t seed, int64_t p, int k) {
+  const uint64_t z = splitmix64(seed ^ ((uint64_t)p * 0x100000001B3ULL) ^ ((uint64_t)k << 40));
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// One elastic-strain path per thread from the undamaged state.  Pass 1
+// (X == nullptr) counts the kept points of each path; pass 2 writes them at
+// the path's offset, in path order.
+__global__ void k_law_paths(LawArgs A, int64_t n_paths, int steps, double emax, double cyc, double ratio2,
+                            uint64_t seed, int32_t *count, const int64_t *offset, float *X, float *Y) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n_paths) return;
+  const bool cyclic = u01(seed, p, 0) < cyc;
+  const double amp = 1.0 - u01(seed, p, 1);
+  double d[6];
+  for (int i = 0; i < 6; ++i) d[i] = (2.0 * u01(seed, p, 2 + i) - 1.0) * (i < 3 ? emax : 2.0 * emax);
+  const double waves = 1.0 + floor(3.0 * u01(seed, p, 8));
+  double h[7] = {1.0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0};
+  int kept = 0;
+  const int64_t o = offset ? offset[p] : 0;
+  for (int k = 0; k < steps; ++k) {
+    const double t = (double)(k + 1) / steps;
+    const double f = cyclic ? sinpi(waves * t) : t;
+    double ee[6];
+    for (int i = 0; i < 6; ++i) ee[i] = amp * f * d[i];
+    const double r2 = cdm_onset_ratio2(A.M, A.L, ee, h);
+    double h2[7], s[6];
+    for (int i = 0; i < 7; ++i) h2[i] = h[i];
+    law_point(A, ee, h2, s);
+    if (r2 <= ratio2) {
+      if (X) {
+        float *x = X + (o + kept) * kIn, *y = Y + (o + kept) * kOut;
+        for (int i = 0; i < 6; ++i) {
+          x[i] = (float)ee[i];
+          y[i] = (float)s[i];
+        }
+        for (int i = 0; i < 4; ++i) {
+          x[6 + i] = (float)h[i];
+          y[6 + i] = (float)h2[i];
+        }
+      }
+      ++kept;
+    }
+    for (int i = 0; i < 7; ++i) h[i] = h2[i];
+  }
+  if (count) count[p] = kept;
+}
+
+__global__ void k_law_points(LawArgs A, const float *in, float *out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ee[6], h[7], s[6];
+  for (int k = 0; k < 6; ++k) ee[k] = in[i * kIn + k];
+  for (int k = 0; k < 4; ++k) h[k] = in[i * kIn + 6 + k];
+  h[4] = h[5] = h[6] = 0.0;
+  law_point(A, ee, h, s);
+  for (int k = 0; k < 6; ++k) out[i * kOut + k] = (float)s[k];
+  for (int k = 0; k < 4; ++k) out[i * kOut + 6 + k] = (float)h[k];
+}
+
+// ---------------------------------------------------------------------------
+// Tile kernels.  Shared memory of a block: the network, then per warp its
+// tiles.
+
+struct WarpTiles {
+  __nv_bfloat16 a0[16 * kS16];      // normalised inputs
+  __nv_bfloat16 a[3][16 * kS64];    // hidden activations (relu), bf16
+  __nv_bfloat16 g16[16 * kS16];     // output-layer gradient, bf16
+  __nv_bfloat16 g64[16 * kS64];     // hidden-layer gradient, bf16
+  float y[16 * kOutPad];            // normalised outputs
+};
+
+__device__ __forceinline__ WarpTiles &warp_tiles(unsigned char *smem) {
+  return reinterpret_cast<WarpTiles *>(smem + sizeof(SmemNet))[threadIdx.x >> 5];
+}
+
+// Normalised bf16 input tile from raw rows (row index of tile row r: idx(r)).
+template <typename IdxF>
+__device__ __forceinline__ void load_inputs(__nv_bfloat16 *a0, const float *X, const Scaling &sc, IdxF idx) {
+  const int l = threadIdx.x & 31;
+  for (int e = l; e < 16 * kInPad; e += 32) {
+    const int r = e / kInPad, c = e % kInPad;
+    float v = 0.0f;
+    if (c < kIn) {
+      const int64_t row = idx(r);
+      v = (X[row * kIn + c] - sc.in_shift[c]) * sc.in_mul[c];
+    }
+    a0[r * kS16 + c] = __float2bfloat16_rn(v);
+  }
+}
+
+// acc[NT][4] = G[16][16*KT] W with W [16*KT][8*NT] stored as W [n][k] row-major
+// (the backward product through a layer: rows of W are the layer's outputs).
+template <int KT, int NT>
+__device__ __forceinline__ void layer_back(const __nv_bfloat16 *G, int gs, const __nv_bfloat16 *W, int ws,
+                                           float (&acc)[NT][4]) {
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt) {
+    uint32_t a[4];
+    ldsm_x4(a, a_ptr(G, gs, kt * 16));
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      uint32_t b[2];
+      ldsm_x2_t(b, W + (kt * 16 + (l & 15)) * ws + nt * 8);
+      mma16816(acc[nt], a, b);
+    }
+  }
+}
+
+// dZ = acc * relu'(z) (the mask is a > 0 of the stored bf16 activation),
+// as fp32 to global rows and as bf16 into the gradient tile.
+template <int NT>
+__device__ __forceinline__ void store_grad(const float (&acc)[NT][4], const __nv_bfloat16 *act, float *dz_out,
+                                           __nv_bfloat16 *g, int gs) {
+  const int l = threadIdx.x & 31, gr = l >> 2, t = l & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const int r = gr + 8 * hf, c = nt * 8 + 2 * t;
+      const float m0 = __bfloat162float(act[r * kS64 + c]) > 0.0f ? 1.0f : 0.0f;
+      const float m1 = __bfloat162float(act[r * kS64 + c + 1]) > 0.0f ? 1.0f : 0.0f;
+      const float v0 = acc[nt][2 * hf] * m0, v1 = acc[nt][2 * hf + 1] * m1;
+      dz_out[r * kHid + c] = v0;
+      dz_out[r * kHid + c + 1] = v1;
+      *reinterpret_cast<__nv_bfloat162 *>(g + r * gs + c) = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+struct TrainBufs {
+  __nv_bfloat16 *A0;      // [B][16]
+  __nv_bfloat16 *A[3];    // [B][64]
+  float *DZ[3];           // [B][64] gradients of the hidden pre-activations
+  float *DY;              // [B][16] gradient of the outputs
+  float *loss_part;       // [B / 16] per tile
+};
+
+// Forward and backward through the activations for B points (one tile of 16
+// per warp): rows idx(i) of X (raw inputs) and T (raw targets), scaled by sc.
+// Loss = mean over points and the kOut outputs of (y_n - t_n)^2.
+__global__ void __launch_bounds__(kWarps * 32) k_train_tiles(const float *params, Scaling sc, const float *X,
+                                                             const float *T, int64_t n_rows, int64_t B,
+                                                             int32_t random, uint64_t seed, TrainBufs tb) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
+  load_net(N, params);
+  __syncthreads();
+  WarpTiles &W = warp_tiles(smem);
+  const int l = threadIdx.x & 31;
+  const int64_t tile = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (tile * 16 >= B) return;
+  auto idx = [&](int r) -> int64_t {
+    const int64_t i = tile * 16 + r;
+    return random ? (int64_t)(splitmix64(seed ^ (uint64_t)i) % (uint64_t)n_rows) : i;
+  };
+  load_inputs(W.a0, X, sc, idx);
+  __syncwarp();
+  {
+    float acc[8][4];
+    layer_fwd<1, 8>(W.a0, kS16, N.W1, kS16, N.b1, acc);
+    store_relu<8>(acc, W.a[0], kS64, nullptr, 0);
+  }
+  __syncwarp();
+  {
+    float acc[8][4];
+    layer_fwd<4, 8>(W.a[0], kS64, N.W2, kS64, N.b2, acc);
+    store_relu<8>(acc, W.a[1], kS64, nullptr, 0);
+  }
+  __syncwarp();
+  {
+    float acc[8][4];
+    layer_fwd<4, 8>(W.a[1], kS64, N.W3, kS64, N.b3, acc);
+    store_relu<8>(acc, W.a[2], kS64, nullptr, 0);
+  }
+  __syncwarp();
+  {
+    float acc[2][4];
+    layer_fwd<4, 2>(W.a[2], kS64, N.W4, kS64, N.b4, acc);
+    store_f32<2>(acc, W.y, kOutPad);
+  }
+  __syncwarp();
+  // output gradient dL/dy_n = 2 (y_n - t_n) / (B kOut), padded columns 0
+  const float gscale = 2.0f / ((float)B * (float)kOut);
+  float lsum = 0.0f;
+  for (int e = l; e < 16 * kOutPad; e += 32) {
+    const int r = e / kOutPad, c = e % kOutPad;
+    float gv = 0.0f;
+    if (c < kOut) {
+      const float tn = (T[idx(r) * kOut + c] - sc.out_shift[c]) / sc.out_mul[c];
+      const float dlt = W.y[r * kOutPad + c] - tn;
+      lsum += dlt * dlt;
+      gv = gscale * dlt;
+    }
+    tb.DY[(tile * 16 + r) * kOutPad + c] = gv;
+    W.g16[r * kS16 + c] = __float2bfloat16_rn(gv);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if (l == 0) tb.loss_part[tile] = lsum / ((float)B * (float)kOut);
+  // the activations for the weight gradients
+  for (int e = l; e < 16 * kInPad; e += 32) {
+    const int r = e / kInPad, c = e % kInPad;
+    tb.A0[(tile * 16 + r) * kInPad + c] = W.a0[r * kS16 + c];
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int e = l; e < 16 * kHid; e += 32) {
+      const int r = e / kHid, c = e % kHid;
+      tb.A[k][(tile * 16 + r) * kHid + c] = W.a[k][r * kS64 + c];
+    }
+  __syncwarp();
+  float *dz3 = tb.DZ[2] + tile * 16 * kHid, *dz2 = tb.DZ[1] + tile * 16 * kHid, *dz1 = tb.DZ[0] + tile * 16 * kHid;
+  {
+    float acc[8][4];
+    layer_back<1, 8>(W.g16, kS16, N.W4, kS64, acc);
+    store_grad<8>(acc, W.a[2], dz3, W.g64, kS64);
+  }
+  __syncwarp();
+  {
+    float acc[8][4];
+    layer_back<4, 8>(W.g64, kS64, N.W3, kS64, acc);
+    __syncwarp();  // every lane has read the gradient tile before it is overwritten
+    store_grad<8>(acc, W.a[1], dz2, W.g64, kS64);
+  }
+  __syncwarp();
+  {
+    float acc[8][4];
+    layer_back<4, 8>(W.g64, kS64, N.W2, kS64, acc);
+    __syncwarp();
+    store_grad<8>(acc, W.a[0], dz1, W.g64, kS64);
+  }
+}
+
+// Weight and bias gradients of one layer over one chunk of kChunk points:
+// dW[n][k] = sum_m dZ[m][n] A[m][k], db[n] = sum_m dZ[m][n], in a fixed
+// order, written as the chunk's partial.
+__global__ void __launch_bounds__(kWarps * 32) k_train_wgrad(TrainBufs tb, int64_t B, float *partW, float *partB,
+                                                             int64_t n_chunks) {
+  __shared__ __align__(16) __nv_bfloat16 sG[kChunk * kS64];
+  __shared__ __align__(16) __nv_bfloat16 sA[kChunk * kS64];
+  const int layer = blockIdx.y;
+  const int64_t chunk = blockIdx.x;
+  const int M = layer_out(layer), K = layer_in(layer);
+  const float *dz = layer == 3 ? tb.DY : tb.DZ[layer];
+  const __nv_bfloat16 *act = layer == 0 ? tb.A0 : tb.A[layer - 1];
+  const int64_t r0 = chunk * kChunk;
+  for (int e = threadIdx.x; e < kChunk * M; e += blockDim.x) {
+    const int r = e / M, c = e % M;
+    sG[r * kS64 + c] = __float2bfloat16_rn(dz[(r0 + r) * M + c]);
+  }
+  for (int e = threadIdx.x; e < kChunk * K; e += blockDim.x) {
+    const int r = e / K, c = e % K;
+    sA[r * kS64 + c] = act[(r0 + r) * K + c];
+  }
+  __syncthreads();
+  float *pW = partW + ((size_t)layer * n_chunks + chunk) * (kHid * kHid);
+  float *pB = partB + ((size_t)layer * n_chunks + chunk) * kHid;
+  for (int c = threadIdx.x; c < M; c += blockDim.x) {
+    float sb = 0.0f;
+    for (int r = 0; r < kChunk; ++r) sb += dz[(r0 + r) * M + c];
+    pB[c] = sb;
+  }
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, g = l >> 2, t = l & 3;
+  const int mt_n = M / 16, nt_n = K / 8;
+  for (int tl = w; tl < mt_n * nt_n; tl += kWarps) {
+    const int n0 = (tl / nt_n) * 16, k0 = (tl % nt_n) * 8;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int s0 = 0; s0 < kChunk; s0 += 16) {
+      uint32_t a[4], b[2];
+      // A = dZ^T (rows: outputs n, columns: points), from dZ stored by point
+      ldsm_x4_t(a, sG + (s0 + (l & 7) + ((l >> 4) & 1) * 8) * kS64 + n0 + ((l >> 3) & 1) * 8);
+      // B = A_prev (rows: points, columns: inputs k)
+      ldsm_x2_t(b, sA + (s0 + (l & 15)) * kS64 + k0);
+      mma16816(acc, a, b);
+    }
+    pW[(n0 + g) * K + k0 + 2 * t] = acc[0];
+    pW[(n0 + g) * K + k0 + 2 * t + 1] = acc[1];
+    pW[(n0 + g + 8) * K + k0 + 2 * t] = acc[2];
+    pW[(n0 + g + 8) * K + k0 + 2 * t + 1] = acc[3];
+  }
+}
+
+// Parameter p of the exchange order -> (layer, row, column or -1 for a bias).
+__device__ __forceinline__ void param_site(int p, int &layer, int &row, int &col) {
+  const int sizes[8] = {kHid * kIn, kHid, kHid * kHid, kHid, kHid * kHid, kHid, kOut * kHid, kOut};
+  const int cols[4] = {kIn, kHid, kHid, kHid};
+  int q = p;
+  for (int s = 0; s < 8; ++s) {
+    if (q < sizes[s]) {
+      layer = s >> 1;
+      if (s & 1) {
+        row = q;
+        col = -1;
+      } else {
+        row = q / cols[layer];
+        col = q % cols[layer];
+      }
+      return;
+    }
+    q -= sizes[s];
+  }
+  layer = row = col = -1;
+}
+
+// Sum of the chunk partials (in chunk order) for every parameter; then an
+// Adam step (lr > 0) and/or the gradient copy.  Thread 0 also sums the loss.
+__global__ void k_train_update(float *params, float *m1, float *m2, float *grad_out, const float *partW,
+                               const float *partB, int64_t n_chunks, float lr, float bc1, float bc2,
+                               const float *loss_part, int64_t n_tiles, double *loss_out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0 && loss_out) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n_tiles; ++i) s += loss_part[i];
+    *loss_out = s;
+  }
+  if (p >= kNumParams) return;
+  int layer, row, col;
+  param_site(p, layer, row, col);
+  const int K = layer_in(layer);
+  float g = 0.0f;
+  for (int64_t c = 0; c < n_chunks; ++c) {
+    const size_t base = (size_t)layer * n_chunks + c;
+    g += col < 0 ? partB[base * kHid + row] : partW[base * (kHid * kHid) + row * K + col];
+  }
+  if (grad_out) grad_out[p] = g;
+  if (lr > 0.0f) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float mm = b1 * m1[p] + (1.0f - b1) * g;
+    const float vv = b2 * m2[p] + (1.0f - b2) * g * g;
+    m1[p] = mm;
+    m2[p] = vv;
+    params[p] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + 1e-8f);
+  }
+}
+
+// Inference on raw points: one tile of 16 per warp.
+__global__ void __launch_bounds__(kWarps * 32) k_sur_forward(const float *params, Scaling sc, const float *in,
+                                                             float *out, int64_t n) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
+  load_net(N, params);
+  __syncthreads();
+  WarpTiles &W = warp_tiles(smem);
+  const int l = threadIdx.x & 31;
+  const int64_t tile = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (tile * 16 >= n) return;
+  auto idx = [&](int r) -> int64_t {
+    const int64_t i = tile * 16 + r;
+    return i < n ? i : n - 1;
+  };
+  load_inputs(W.a0, in, sc, idx);
+  __syncwarp();
+  warp_forward16(N, W.a0, W.a[0], W.a[1], W.y, kOutPad, nullptr);
+  for (int e = l; e < 16 * kOut; e += 32) {
+    const int r = e / kOut, c = e % kOut;
+    const int64_t i = tile * 16 + r;
+    if (i < n) out[i * kOut + c] = W.y[r * kOutPad + c] * sc.out_mul[c] + sc.out_shift[c];
+  }
+}
+
+// He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases.
+__global__ void k_init_params(float *p, uint64_t seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kNumParams) return;
+  int layer, row, col;
+  param_site(i, layer, row, col);
+  if (col < 0) {
+    p[i] = 0.0f;
+    return;
+  }
+  const float fan_in = (float)(layer == 0 ? kIn : kHid);
+  const double u = (double)(splitmix64(seed ^ (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+  p[i] = (float)((2.0 * u - 1.0) * sqrt(6.0 / fan_in));
+}
+
+// ---------------------------------------------------------------------------
+// Hex8 of an axis-aligned box (FP32) with the learned law where it applies.
+// Same formulation and arithmetic as the scalar element of pdn_items.cuh
+// (Eq. fcont, Algorithm 4); at each Gauss point the exact plasticity runs
+// first, then either the network (all loading-function ratios at most the
+// context's onset ratio and every input inside the training box: the
+// thresholds do not change there) or the exact damage part.  The network
+// runs once per point index for the 32 points of a warp (two 16-point tiles)
+// whenever any lane needs it; lanes past the last element follow the same
+// control flow on a valid element and store nothing.
+
+struct HexSurTiles {
+  __nv_bfloat16 x[2][16 * kS16];
+  __nv_bfloat16 h0[16 * kS64], h1[16 * kS64];
+  float y[2][16 * kOutPad];
+};
+constexpr int kHexSurBlock = 128;
+constexpr size_t kHexSurSmem = sizeof(SmemNet) + sizeof(Scaling) + (kHexSurBlock / 32) * sizeof(HexSurTiles);
+static_assert(sizeof(Scaling) == PDN_SUR_SCALING * sizeof(float), "scaling record of 60 floats");
+static_assert(sizeof(SmemNet) % 16 == 0 && sizeof(Scaling) % 16 == 0, "16-byte aligned shared tiles");
+
+__global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<float> M) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
+  Scaling &sc = *reinterpret_cast<Scaling *>(smem + sizeof(SmemNet));
+  HexSurTiles &Wt = reinterpret_cast<HexSurTiles *>(smem + sizeof(SmemNet) + sizeof(Scaling))[threadIdx.x >> 5];
+  const Ctl *ctl = D.ctl;
+  const int mode = ctl->mode;
+  if (mode >= MODE_DONE) return;
+  load_net(N, D.sur_params);
+  for (int k = threadIdx.x; k < PDN_SUR_SCALING; k += blockDim.x)
+    reinterpret_cast<float *>(&sc)[k] = D.sur_params[kNumParams + k];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nh = D.nh;
+  if (e - lane >= nh) return;  // the whole warp is past the last element
+  const bool act = e < nh;
+  const int64_t el = act ? e : nh - 1;
+  const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+  const int hb = ctl->hpar;
+  const float4 *__restrict__ U = D.u4[ub];
+  const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * el);
+  const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * el + 1);
+  const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  const float *__restrict__ hin = D.hist[hb] + el;
+  float *__restrict__ hout = D.hist[hb ^ 1] + el;
+  const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][el] != 0;
+  bool dirty = false;
+  float bm[8][3], jd[3], wd[3], vol;
+  {
+    float ua[8][3];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const float4 u = U[nd[a]];
+      ua[a][0] = u.x;
+      ua[a][1] = u.y;
+      ua[a][2] = u.z;
+    }
+    to_modes(ua, bm);
+    const float4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
+    const float J0 = 0.5f * (x6.x - x0.x), J1 = 0.5f * (x6.y - x0.y), J2 = 0.5f * (x6.z - x0.z);
+    const float det = J0 * (J1 * J2);
+    jd[0] = 1.0f / J0;
+    jd[1] = 1.0f / J1;
+    jd[2] = 1.0f / J2;
+    wd[0] = det * jd[0];
+    wd[1] = det * jd[1];
+    wd[2] = det * jd[2];
+    vol = 8.0f * det;
+  }
+  const int ply = D.ply[el];
+  const float cs = M.ply_c[ply], sn = M.ply_s[ply];
+  const float c2 = cs * cs, s2 = sn * sn, csn = cs * sn;
+  const ElemLaw<float> L = elem_law(M, el);
+  float lc = -1.0f;
+  float C[8][3];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) C[m][0] = C[m][1] = C[m][2] = 0.0f;
+  const float gp = 0.57735026918962576451f;
+  const int tl = lane >> 4, row = lane & 15;
+#pragma unroll 1
+  for (int g = 0; g < 8; ++g) {
+    float h[7];
+#pragma unroll
+    for (int f = 0; f < 7; ++f) h[f] = pristine_in ? (f < 4 ? 1.0f : 0.0f) : hin[(int64_t)(f * 8 + g) * nh];
+    const float xi = float(sgn_x(g)) * gp, et = float(sgn_y(g)) * gp, ze = float(sgn_z(g)) * gp;
+    float Du[3][3], H[3][3];
+    jac_cols(bm, xi, et, ze, Du);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) H[i][k] = Du[i][k] * jd[k];
+    float E[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = i; k < 3; ++k) {
+        E[i][k] = 0.5f * (H[i][k] + H[k][i] + H[0][i] * H[0][k] + H[1][i] * H[1][k] + H[2][i] * H[2][k]);
+        E[k][i] = E[i][k];
+      }
+    float ep[6];
+    ep[0] = c2 * E[0][0] + 2.0f * csn * E[0][1] + s2 * E[1][1];
+    ep[1] = s2 * E[0][0] - 2.0f * csn * E[0][1] + c2 * E[1][1];
+    ep[2] = E[2][2];
+    ep[3] = 2.0f * (-csn * E[0][0] + (c2 - s2) * E[0][1] + csn * E[1][1]);
+    ep[4] = 2.0f * (cs * E[0][2] + sn * E[1][2]);
+    ep[5] = 2.0f * (-sn * E[0][2] + cs * E[1][2]);
+    cdm_plastic(M, ep, h);
+    const float eel[6] = {ep[0], ep[1], ep[2], ep[3] - h[4], ep[4] - h[5], ep[5]};
+    bool inbox = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) inbox = inbox && eel[k] >= sc.lo[k] && eel[k] <= sc.hi[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) inbox = inbox && h[k] >= sc.lo[6 + k] && h[k] <= sc.hi[6 + k];
+    const bool use = act && inbox && cdm_onset_ratio2(M, L, eel, h) <= D.sur_ratio2;
+    float sm[6];
+    if (__any_sync(0xffffffffu, use)) {
+      __nv_bfloat16 *xr = Wt.x[tl] + row * kS16;
+#pragma unroll
+      for (int c = 0; c < kInPad; c += 2) {
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int cc = c + q;
+          const float raw = cc < 6 ? eel[cc] : (cc < kIn ? h[cc - 6] : 0.0f);
+          v[q] = cc < kIn ? (raw - sc.in_shift[cc]) * sc.in_mul[cc] : 0.0f;
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(xr + c) = __floats2bfloat162_rn(v[0], v[1]);
+      }
+      __syncwarp();
+      warp_forward16(N, Wt.x[0], Wt.h0, Wt.h1, Wt.y[0], kOutPad, nullptr);
+      warp_forward16(N, Wt.x[1], Wt.h0, Wt.h1, Wt.y[1], kOutPad, nullptr);
+      if (use) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) sm[k] = Wt.y[tl][row * kOutPad + k] * sc.out_mul[k] + sc.out_shift[k];
+      }
+      __syncwarp();
+    }
+    if (!use) cdm_damage(M, L, (const float(*)[3]) nullptr, vol, lc, ep, h, sm);
+    if (act) {
+      if (!pristine_in) {
+#pragma unroll
+        for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + g) * nh] = h[f];
+      } else {
+        const bool changed = h[0] > 1.0f || h[1] > 1.0f || h[2] > 1.0f || h[3] > 1.0f || h[4] != 0.0f ||
+                             h[5] != 0.0f || h[6] != 0.0f;
+        if (changed && !dirty) {
+          for (int gg = 0; gg < g; ++gg)
+#pragma unroll
+            for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + gg) * nh] = f < 4 ? 1.0f : 0.0f;
+          dirty = true;
+        }
+        if (dirty) {
+#pragma unroll
+          for (int f = 0; f < 7; ++f) hout[(int64_t)(f * 8 + g) * nh] = h[f];
+        }
+      }
+    }
+    float S[3][3];
+    S[0][0] = c2 * sm[0] - 2.0f * csn * sm[3] + s2 * sm[1];
+    S[1][1] = s2 * sm[0] + 2.0f * csn * sm[3] + c2 * sm[1];
+    S[2][2] = sm[2];
+    S[0][1] = S[1][0] = csn * sm[0] + (c2 - s2) * sm[3] - csn * sm[1];
+    S[0][2] = S[2][0] = cs * sm[4] - sn * sm[5];
+    S[1][2] = S[2][1] = sn * sm[4] + cs * sm[5];
+    float Q[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int I = 0; I < 3; ++I)
+        Q[k][I] = wd[k] * (S[k][I] + S[k][0] * H[I][0] + S[k][1] * H[I][1] + S[k][2] * H[I][2]);
+#pragma unroll
+    for (int I = 0; I < 3; ++I) {
+      C[1][I] += Q[0][I];
+      C[2][I] += Q[1][I];
+      C[3][I] += Q[2][I];
+      C[4][I] += et * Q[0][I] + xi * Q[1][I];
+      C[5][I] += ze * Q[1][I] + et * Q[2][I];
+      C[6][I] += ze * Q[0][I] + xi * Q[2][I];
+      C[7][I] += et * ze * Q[0][I] + xi * ze * Q[1][I] + xi * et * Q[2][I];
+    }
+  }
+  if (!act) return;
+  if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][el] = (pristine_in && !dirty) ? 1 : 0;
+  float f[8][3];
+  from_modes(C, f);
+  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * el);
+  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * el + 1);
+  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+#pragma unroll
+  for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
+}
+
+thread_local std::string g_sur_error;
+
+}  // namespace
+}  // namespace pdn
+
+namespace pdn {
+cudaError_t launch_hex_sur(const Dev<float> &D, const Mat<float> &M, cudaStream_t s) {
+  const int64_t g = (D.nh + kHexSurBlock - 1) / kHexSurBlock;
+  k_hex_sur<<<(unsigned)(g < 1 ? 1 : g), kHexSurBlock, kHexSurSmem, s>>>(D, M);
+  return cudaGetLastError();
+}
+}  // namespace pdn
+
+using namespace pdn;
+using namespace pdn::mlp;
+
+struct pdn_surrogate {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  LawArgs law{};
+  Scaling sc{};
+  float *params = nullptr, *m1 = nullptr, *m2 = nullptr;  // device, kNumParams each
+  int64_t adam_t = 0;
+  // training set
+  float *X = nullptr, *Y = nullptr;
+  int64_t n = 0;
+  // work buffers for a minibatch of cap points
+  int64_t cap = 0;
+  TrainBufs tb{};
+  float *partW = nullptr, *partB = nullptr, *grad = nullptr;
+  double *loss_dev = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int sfail(pdn_surrogate *s, int code, const std::string &m) {
+  if (s) s->err = m;
+  return code;
+}
+int scuda(pdn_surrogate *s, cudaError_t e, const char *where) {
+  return sfail(s, PDN_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define PS_CU(call, where)                             \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return scuda(s, _e, where); \
+  } while (0)
+
+constexpr size_t kTileSmem = sizeof(SmemNet) + kWarps * sizeof(WarpTiles);
+
+void free_bufs(pdn_surrogate *s) {
+  cudaFree(s->tb.A0);
+  for (int k = 0; k < 3; ++k) {
+    cudaFree(s->tb.A[k]);
+    cudaFree(s->tb.DZ[k]);
+  }
+  cudaFree(s->tb.DY);
+  cudaFree(s->tb.loss_part);
+  cudaFree(s->partW);
+  cudaFree(s->partB);
+  s->tb = TrainBufs{};
+  s->partW = s->partB = nullptr;
+  s->cap = 0;
+}
+
+int ensure_bufs(pdn_surrogate *s, int64_t B) {
+  if (B <= s->cap) return PDN_OK;
+  free_bufs(s);
+  const int64_t nch = B / kChunk;
+  PS_CU(cudaMalloc(&s->tb.A0, sizeof(__nv_bfloat16) * B * kInPad), "surrogate buffers");
+  for (int k = 0; k < 3; ++k) {
+    PS_CU(cudaMalloc(&s->tb.A[k], sizeof(__nv_bfloat16) * B * kHid), "surrogate buffers");
+    PS_CU(cudaMalloc(&s->tb.DZ[k], sizeof(float) * B * kHid), "surrogate buffers");
+  }
+  PS_CU(cudaMalloc(&s->tb.DY, sizeof(float) * B * kOutPad), "surrogate buffers");
+  PS_CU(cudaMalloc(&s->tb.loss_part, sizeof(float) * (B / 16)), "surrogate buffers");
+  PS_CU(cudaMalloc(&s->partW, sizeof(float) * kLayers * nch * kHid * kHid), "surrogate buffers");
+  PS_CU(cudaMalloc(&s->partB, sizeof(float) * kLayers * nch * kHid), "surrogate buffers");
+  s->cap = B;
+  return PDN_OK;
+}
+
+// One forward/backward over B points (rows of X/T; random: seeded draws),
+// weight gradients, then the update (lr > 0: Adam) and/or gradient copy.
+int train_step(pdn_surrogate *s, const Scaling &sc, const float *X, const float *T, int64_t n_rows, int64_t B,
+               int random, uint64_t seed, float lr, float *grad_out, double *loss_out) {
+  int rc = ensure_bufs(s, B);
+  if (rc) return rc;
+  const int64_t tiles = B / 16, nch = B / kChunk;
+  k_train_tiles<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, kTileSmem, s->stream>>>(
+      s->params, sc, X, T, n_rows, B, random, seed, s->tb);
+  PS_CU(cudaGetLastError(), "train tiles");
+  k_train_wgrad<<<dim3((unsigned)nch, kLayers), kWarps * 32, 0, s->stream>>>(s->tb, B, s->partW, s->partB, nch);
+  PS_CU(cudaGetLastError(), "weight gradients");
+  float bc1 = 1.0f, bc2 = 1.0f;
+  if (lr > 0.0f) {
+    ++s->adam_t;
+    bc1 = 1.0f - std::pow(0.9f, (float)s->adam_t);
+    bc2 = 1.0f - std::pow(0.999f, (float)s->adam_t);
+  }
+  k_train_update<<<(kNumParams + 255) / 256, 256, 0, s->stream>>>(s->params, s->m1, s->m2, grad_out, s->partW,
+                                                                    s->partB, nch, lr, bc1, bc2, s->tb.loss_part,
+                                                                    tiles, loss_out);
+  PS_CU(cudaGetLastError(), "update");
+  return PDN_OK;
+}
+
+Scaling identity_scaling() {
+  Scaling sc{};
+  for (int i = 0; i < kIn; ++i) {
+    sc.in_shift[i] = 0.0f;
+    sc.in_mul[i] = 1.0f;
+    sc.lo[i] = -1e30f;
+    sc.hi[i] = 1e30f;
+  }
+  for (int i = 0; i < kOut; ++i) {
+    sc.out_shift[i] = 0.0f;
+    sc.out_mul[i] = 1.0f;
+  }
+  return sc;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pdn_sur_last_error(const pdn_surrogate *s) { return s ? s->err.c_str() : g_sur_error.c_str(); }
+
+void pdn_sur_destroy(pdn_surrogate *s) {
+  if (!s) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_bufs(s);
+  cudaFree(s->params);
+  cudaFree(s->m1);
+  cudaFree(s->m2);
+  cudaFree(s->X);
+  cudaFree(s->Y);
+  cudaFree(s->grad);
+  cudaFree(s->loss_dev);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  cudaSetDevice(prev);
+  delete s;
+}
+
+int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint64_t seed, void *stream) {
+  g_sur_error.clear();
+  if (!out) {
+    g_sur_error = "out is NULL";
+    return PDN_E_ARG;
+  }
+  *out = nullptr;
+  if (!mat || !(lc > 0.0)) {
+    g_sur_error = "a material and lc > 0 are required";
+    return PDN_E_ARG;
+  }
+  pdn_surrogate *s = new (std::nothrow) pdn_surrogate();
+  if (!s) {
+    g_sur_error = "host allocation failed";
+    return PDN_E_OOM;
+  }
+  auto bad = [&](int code, const std::string &m) {
+    g_sur_error = m;
+    pdn_sur_destroy(s);
+    return code;
+  };
+  cudaGetDevice(&s->device);
+  std::string why;
+  const double zero_angle = 0.0;
+  int rc = fill_mat_public(s->law.M, *mat, &zero_angle, 1, 1, 0, why);
+  if (rc) return bad(rc, why);
+  Mat<double> &M = s->law.M;
+  s->law.L.XT = M.XT;
+  s->law.L.YT = M.YT;
+  s->law.L.SL = M.SL;
+  s->law.L.iXT = 1.0 / M.XT;
+  s->law.L.iYT = 1.0 / M.YT;
+  s->law.L.iSL2 = 1.0 / (M.SL * M.SL);
+  s->law.L.etaL = M.SL * M.etaLc;
+  s->law.lc = lc;
+  // the crack band must not snap back at this length (as pdn_init_mesh checks)
+  const double X[5] = {M.XT, M.XC, M.YT, M.YC, M.SL}, E[5] = {M.E1, M.E1, M.E2, M.E2, M.G12},
+               G[5] = {M.GXT, M.GXC, M.GYT, M.GYC, M.GSL};
+  for (int k = 0; k < 5; ++k)
+    if (!(2.0 * E[k] * G[k] - lc * X[k] * X[k] > 0.0))
+      return bad(PDN_E_UNSTABLE, "crack-band length too large for this material (snap-back)");
+  s->sc = identity_scaling();
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bad(PDN_E_CUDA, "stream create failed");
+    s->own_stream = true;
+  }
+  if (cudaMalloc(&s->params, sizeof(float) * kNumParams) != cudaSuccess ||
+      cudaMalloc(&s->m1, sizeof(float) * kNumParams) != cudaSuccess ||
+      cudaMalloc(&s->m2, sizeof(float) * kNumParams) != cudaSuccess ||
+      cudaMalloc(&s->grad, sizeof(float) * kNumParams) != cudaSuccess ||
+      cudaMalloc(&s->loss_dev, sizeof(double) * 1) != cudaSuccess)
+    return bad(PDN_E_OOM, "surrogate parameters");
+  cudaMemsetAsync(s->m1, 0, sizeof(float) * kNumParams, s->stream);
+  cudaMemsetAsync(s->m2, 0, sizeof(float) * kNumParams, s->stream);
+  k_init_params<<<(kNumParams + 255) / 256, 256, 0, s->stream>>>(s->params, seed);
+  if (cudaFuncSetAttribute(k_train_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k_sur_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) != cudaSuccess)
+    return bad(PDN_E_CUDA, "shared-memory attribute");
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bad(PDN_E_CUDA, "surrogate init");
+  *out = s;
+  return PDN_OK;
+}
+
+int pdn_sur_generate(pdn_surrogate *s, int64_t n_paths, int32_t steps, double strain_max, double cyclic_fraction,
+                     double onset_ratio, uint64_t seed, int64_t *n_kept) {
+  if (!s) return PDN_E_ARG;
+  if (n_paths < 1 || steps < 1 || steps > 1024 || !(strain_max > 0.0) || !(onset_ratio > 0.0) ||
+      !(cyclic_fraction >= 0.0 && cyclic_fraction <= 1.0))
+    return sfail(s, PDN_E_ARG, "bad path parameters");
+  int32_t *cnt = nullptr;
+  int64_t *off = nullptr;
+  PS_CU(cudaMalloc(&cnt, sizeof(int32_t) * n_paths), "path counts");
+  const double r2 = onset_ratio * onset_ratio;
+  const unsigned grid = (unsigned)((n_paths + 127) / 128);
+  k_law_paths<<<grid, 128, 0, s->stream>>>(s->law, n_paths, steps, strain_max, cyclic_fraction, r2, seed, cnt,
+                                           nullptr, nullptr, nullptr);
+  std::vector<int32_t> hc(n_paths);
+  cudaError_t e = cudaMemcpyAsync(hc.data(), cnt, sizeof(int32_t) * n_paths, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    cudaFree(cnt);
+    return scuda(s, e, "count pass");
+  }
+  std::vector<int64_t> ho(n_paths);
+  int64_t tot = 0;
+  for (int64_t p = 0; p < n_paths; ++p) {
+    ho[p] = tot;
+    tot += hc[p];
+  }
+  if (tot < 128) {
+    cudaFree(cnt);
+    return sfail(s, PDN_E_ARG, "fewer than 128 points in the surrogate regime");
+  }
+  cudaFree(s->X);
+  cudaFree(s->Y);
+  s->X = s->Y = nullptr;
+  s->n = 0;
+  e = cudaMalloc(&off, sizeof(int64_t) * n_paths);
+  if (e == cudaSuccess) e = cudaMalloc(&s->X, sizeof(float) * kIn * tot);
+  if (e == cudaSuccess) e = cudaMalloc(&s->Y, sizeof(float) * kOut * tot);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(off, ho.data(), sizeof(int64_t) * n_paths, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) {
+    k_law_paths<<<grid, 128, 0, s->stream>>>(s->law, n_paths, steps, strain_max, cyclic_fraction, r2, seed, nullptr,
+                                             off, s->X, s->Y);
+    e = cudaGetLastError();
+  }
+  std::vector<float> hx, hy;
+  if (e == cudaSuccess) {
+    hx.resize((size_t)kIn * tot);
+    hy.resize((size_t)kOut * tot);
+    e = cudaMemcpyAsync(hx.data(), s->X, sizeof(float) * kIn * tot, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hy.data(), s->Y, sizeof(float) * kOut * tot, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  }
+  cudaFree(cnt);
+  cudaFree(off);
+  if (e != cudaSuccess) return scuda(s, e, "training set");
+  s->n = tot;
+  // scaling: mean and spread of the kept points; box: their range
+  Scaling sc{};
+  for (int c = 0; c < kIn; ++c) {
+    double m = 0.0, q = 0.0, lo = 1e300, hi = -1e300;
+    for (int64_t i = 0; i < tot; ++i) {
+      const double v = hx[i * kIn + c];
+      m += v;
+      q += v * v;
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+    m /= tot;
+    const double sd = std::sqrt(std::max(q / tot - m * m, 0.0));
+    const double floor = c < 6 ? 1e-7 : 1e-3;
+    sc.in_shift[c] = (float)m;
+    sc.in_mul[c] = (float)(1.0 / std::max(sd, floor));
+    sc.lo[c] = (float)lo;
+    sc.hi[c] = (float)hi;
+  }
+  for (int c = 0; c < kOut; ++c) {
+    double m = 0.0, q = 0.0;
+    for (int64_t i = 0; i < tot; ++i) {
+      const double v = hy[i * kOut + c];
+      m += v;
+      q += v * v;
+    }
+    m /= tot;
+    const double sd = std::sqrt(std::max(q / tot - m * m, 0.0));
+    sc.out_shift[c] = (float)m;
+    sc.out_mul[c] = (float)std::max(sd, c < 6 ? 1e-3 : 1e-3);
+  }
+  s->sc = sc;
+  if (n_kept) *n_kept = tot;
+  return PDN_OK;
+}
+
+int pdn_sur_get_data(pdn_surrogate *s, int64_t offset, int64_t n, float *x, float *y) {
+  if (!s) return PDN_E_ARG;
+  if (offset < 0 || n < 0 || offset + n > s->n) return sfail(s, PDN_E_ARG, "range outside the training set");
+  if (n == 0) return PDN_OK;
+  if (x) PS_CU(cudaMemcpyAsync(x, s->X + offset * kIn, sizeof(float) * kIn * n, cudaMemcpyDeviceToHost, s->stream), "read set");
+  if (y) PS_CU(cudaMemcpyAsync(y, s->Y + offset * kOut, sizeof(float) * kOut * n, cudaMemcpyDeviceToHost, s->stream), "read set");
+  PS_CU(cudaStreamSynchronize(s->stream), "read set");
+  return PDN_OK;
+}
+
+int pdn_sur_train(pdn_surrogate *s, int64_t iters, int32_t batch, double lr, uint64_t seed, double *loss) {
+  if (!s) return PDN_E_ARG;
+  if (iters < 0 || batch < kChunk || batch % kChunk || !(lr > 0.0)) return sfail(s, PDN_E_ARG, "bad training parameters");
+  if (s->n < kChunk) return sfail(s, PDN_E_STATE, "no training set (pdn_sur_generate)");
+  std::vector<double> lh;
+  double *ld = nullptr;
+  if (loss) PS_CU(cudaMalloc(&ld, sizeof(double) * std::max<int64_t>(iters, 1)), "loss buffer");
+  for (int64_t it = 0; it < iters; ++it) {
+    const double frac = iters > 1 ? (double)it / (double)(iters - 1) : 0.0;
+    const double lr_it = lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac)));
+    const uint64_t sd = splitmix64(seed + 0x51ED270B2A3F1C07ULL * (uint64_t)(it + 1));
+    int rc = train_step(s, s->sc, s->X, s->Y, s->n, batch, 1, sd, (float)lr_it, nullptr, ld ? ld + it : nullptr);
+    if (rc) {
+      cudaFree(ld);
+      return rc;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (ld && iters > 0) e = cudaMemcpyAsync(loss, ld, sizeof(double) * iters, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(ld);
+  if (e != cudaSuccess) return scuda(s, e, "training");
+  return PDN_OK;
+}
+
+int pdn_sur_gradient(pdn_surrogate *s, const float *xn, const float *tn, int64_t n, float *grad, double *loss) {
+  if (!s) return PDN_E_ARG;
+  if (!xn || !tn || !grad || n < kChunk || n % kChunk) return sfail(s, PDN_E_ARG, "need n a multiple of 128 and host arrays");
+  float *dx = nullptr, *dt = nullptr;
+  PS_CU(cudaMalloc(&dx, sizeof(float) * kIn * n), "gradient inputs");
+  cudaError_t e = cudaMalloc(&dt, sizeof(float) * kOut * n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dx, xn, sizeof(float) * kIn * n, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tn, sizeof(float) * kOut * n, cudaMemcpyHostToDevice, s->stream);
+  int rc = PDN_OK;
+  if (e == cudaSuccess) rc = train_step(s, identity_scaling(), dx, dt, n, n, 0, 0, 0.0f, s->grad, s->loss_dev);
+  if (e == cudaSuccess && rc == PDN_OK)
+    e = cudaMemcpyAsync(grad, s->grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s->stream);
+  double lh = 0.0;
+  if (e == cudaSuccess && rc == PDN_OK) e = cudaMemcpyAsync(&lh, s->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(dx);
+  cudaFree(dt);
+  if (rc) return rc;
+  if (e != cudaSuccess) return scuda(s, e, "gradient");
+  if (loss) *loss = lh;
+  return PDN_OK;
+}
+
+static int sur_points(pdn_surrogate *s, const float *in, float *out, int64_t n, int32_t on_device, bool exact) {
+  if (!s) return PDN_E_ARG;
+  if (!in || !out || n < 0) return sfail(s, PDN_E_ARG, "bad point arrays");
+  if (n == 0) return PDN_OK;
+  const float *din = in;
+  float *dout = out;
+  float *tmp_in = nullptr, *tmp_out = nullptr;
+  if (!on_device) {
+    PS_CU(cudaMalloc(&tmp_in, sizeof(float) * kIn * n), "point buffers");
+    PS_CU(cudaMalloc(&tmp_out, sizeof(float) * kOut * n), "point buffers");
+    PS_CU(cudaMemcpyAsync(tmp_in, in, sizeof(float) * kIn * n, cudaMemcpyHostToDevice, s->stream), "copy points");
+    din = tmp_in;
+    dout = tmp_out;
+  }
+  if (exact) {
+    k_law_points<<<(unsigned)((n + 127) / 128), 128, 0, s->stream>>>(s->law, din, dout, n);
+  } else {
+    const int64_t tiles = (n + 15) / 16;
+    k_sur_forward<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, kTileSmem, s->stream>>>(s->params, s->sc,
+                                                                                                    din, dout, n);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(out, dout, sizeof(float) * kOut * n, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(tmp_in);
+  cudaFree(tmp_out);
+  if (e != cudaSuccess) return scuda(s, e, exact ? "exact law" : "surrogate forward");
+  return PDN_OK;
+}
+
+int pdn_sur_forward(pdn_surrogate *s, const float *in, float *out, int64_t n, int32_t on_device) {
+  return sur_points(s, in, out, n, on_device, false);
+}
+
+int pdn_sur_exact(pdn_surrogate *s, const float *in, float *out, int64_t n, int32_t on_device) {
+  return sur_points(s, in, out, n, on_device, true);
+}
+
+int pdn_sur_get_params(pdn_surrogate *s, float *params, float *scaling) {
+  if (!s) return PDN_E_ARG;
+  if (params) {
+    PS_CU(cudaMemcpyAsync(params, s->params, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s->stream), "read params");
+    PS_CU(cudaStreamSynchronize(s->stream), "read params");
+  }
+  if (scaling) std::memcpy(scaling, &s->sc, sizeof(float) * PDN_SUR_SCALING);
+  return PDN_OK;
+}
+
+int pdn_set_surrogate(pdn_ctx *ctx, pdn_surrogate *s, double onset_ratio) {
+  if (!ctx) return PDN_E_ARG;
+  if (!s) {
+    ctx->Df.sur_params = nullptr;
+    return PDN_OK;
+  }
+  if (ctx->precision != PDN_FP32_FORCE || !ctx->Df.all_boxes) {
+    ctx->err = "the learned law needs FP32 element mode and axis-aligned box elements";
+    return PDN_E_ARG;
+  }
+  if (!(onset_ratio > 0.0 && onset_ratio <= 1.0)) {
+    ctx->err = "onset_ratio must be in (0, 1]";
+    return PDN_E_ARG;
+  }
+  if (cudaFuncSetAttribute(k_hex_sur, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHexSurSmem) != cudaSuccess) {
+    ctx->err = "shared-memory attribute of the learned-law hex kernel";
+    return PDN_E_CUDA;
+  }
+  if (!ctx->sur_buf) {
+    if (cudaMalloc(&ctx->sur_buf, sizeof(float) * (kNumParams + PDN_SUR_SCALING)) != cudaSuccess) {
+      ctx->err = "learned-law parameters";
+      return PDN_E_OOM;
+    }
+  }
+  // the context's copy: parameters, then the scaling, on the context's stream
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->sur_buf, s->params, sizeof(float) * kNumParams, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ctx->sur_buf + kNumParams, &s->sc, sizeof(float) * PDN_SUR_SCALING, cudaMemcpyHostToDevice,
+                        ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    ctx->err = std::string("learned-law parameters: ") + cudaGetErrorString(e);
+    return PDN_E_CUDA;
+  }
+  ctx->Df.sur_params = ctx->sur_buf;
+  ctx->Df.sur_ratio2 = (float)(onset_ratio * onset_ratio);
+  // the captured graph holds the old kernel choice
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return PDN_OK;
+}
+
+int pdn_sur_set_params(pdn_surrogate *s, const float *params, const float *scaling) {
+  if (!s) return PDN_E_ARG;
+  if (params) {
+    PS_CU(cudaMemcpyAsync(s->params, params, sizeof(float) * kNumParams, cudaMemcpyHostToDevice, s->stream), "write params");
+    PS_CU(cudaStreamSynchronize(s->stream), "write params");
+  }
+  if (scaling) std::memcpy(&s->sc, scaling, sizeof(float) * PDN_SUR_SCALING);
+  return PDN_OK;
+}
+
+}  // extern "C"

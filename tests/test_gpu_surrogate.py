@@ -1,0 +1,167 @@
+"""Learned surrogate of the intralaminar law (include/pdn_surrogate.h).
+
+* The GPU gradient (BF16 tensor-core products, FP32 sums) equals FP64
+  backpropagation with the same BF16 rounding points (tests/mlp_reference.py,
+  itself pinned by finite differences) to FP32 round-off, and plain FP64
+  backpropagation to the BF16 precision.
+* The exact law that generates the training data equals the FP64 oracle's
+  point law.
+* Generated points lie in the surrogate's regime (no threshold grows).
+"""
+import numpy as np
+import pytest
+
+import mlp_reference as R
+import oracle
+import pdn_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2301_05552_gb300 as p
+    p.lib()
+    return p
+
+
+def _mat():
+    return pi.material_im7_like_config(t_ply=0.275, spread=0.0)
+
+
+LC = 0.552  # crack-band length of the 128x192x16 plate's elements (mm)
+
+
+def _blocks(g):
+    out, o = [], 0
+    for s in R.SHAPES:
+        n = int(np.prod(s))
+        out.append(g[o:o + n])
+        o += n
+    return out
+
+
+def test_gradient_matches_fp64_backprop(pkg):
+    s = pkg.pdn_sur_create(_mat(), LC, seed=7)
+    p, _ = pkg.pdn_sur_get_params(s)
+    rng = np.random.default_rng(1)
+    n = 256
+    xn = rng.normal(size=(n, 10)).astype(np.float32)
+    tn = rng.normal(size=(n, 10)).astype(np.float32)
+    g, loss = pkg.pdn_sur_gradient(s, xn, tn)
+    p64 = p.astype(np.float64)
+    lb, gb = R.loss_and_grad(p64, xn.astype(np.float64), tn.astype(np.float64), bf=True)
+    l64, g64 = R.loss_and_grad(p64, xn.astype(np.float64), tn.astype(np.float64), bf=False)
+    assert abs(loss - lb) <= 1e-5 * lb
+    assert abs(loss - l64) <= 2e-2 * l64
+    for gg, rb, r64 in zip(_blocks(g.astype(np.float64)), _blocks(gb), _blocks(g64)):
+        nb = np.linalg.norm(rb)
+        assert np.linalg.norm(gg - rb) <= 2e-3 * nb + 1e-12
+        assert np.linalg.norm(gg - r64) <= 5e-2 * np.linalg.norm(r64) + 1e-12
+    # the parameters did not move
+    p2, _ = pkg.pdn_sur_get_params(s)
+    assert np.array_equal(p, p2)
+    s.close()
+
+
+def test_exact_law_matches_oracle_point_law(pkg):
+    s = pkg.pdn_sur_create(_mat(), LC, seed=0)
+    rng = np.random.default_rng(2)
+    n = 400
+    x = np.zeros((n, 10), dtype=np.float32)
+    x[:, :3] = rng.uniform(-0.02, 0.02, size=(n, 3))
+    x[:, 3:6] = rng.uniform(-0.04, 0.04, size=(n, 3))
+    x[:, 6:] = np.where(rng.uniform(size=(n, 4)) < 0.5, 1.0, rng.uniform(1.0, 3.0, size=(n, 4)))
+    y = pkg.pdn_sur_exact(s, x)
+    mat = _mat()
+    for i in range(n):
+        h = np.array([*x[i, 6:].astype(np.float64), 0.0, 0.0, 0.0])
+        sig, ho = oracle.cdm_point(mat, LC, x[i, :6].astype(np.float64), h, damage_on=True, plasticity_on=False)
+        scale = max(np.abs(sig).max(), 1.0)
+        assert np.abs(y[i, :6] - sig).max() <= 1e-5 * scale, i
+        assert np.allclose(y[i, 6:], ho[:4], rtol=1e-6), i
+    s.close()
+
+
+def test_generated_points_are_in_the_regime_and_deterministic(pkg):
+    s1 = pkg.pdn_sur_create(_mat(), LC)
+    s2 = pkg.pdn_sur_create(_mat(), LC)
+    n1 = pkg.pdn_sur_generate(s1, 3000, 8, 0.01, 0.4, 0.9, seed=5)
+    n2 = pkg.pdn_sur_generate(s2, 3000, 8, 0.01, 0.4, 0.9, seed=5)
+    assert n1 == n2 and 0.2 * 3000 * 8 < n1 <= 3000 * 8
+    x1, y1 = pkg.pdn_sur_get_data(s1, 0, n1)
+    x2, y2 = pkg.pdn_sur_get_data(s2, 0, n1)
+    assert np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    # no threshold grows in the regime, and thresholds start at 1
+    assert np.array_equal(x1[:, 6:], y1[:, 6:])
+    assert (x1[:, 6:] >= 1.0).all()
+    # some kept points are damaged (thresholds above 1: unloading after onset)
+    assert (x1[:, 6:] > 1.0).any()
+    # the exact law reproduces the stored targets
+    yy = pkg.pdn_sur_exact(s1, x1[:2000])
+    assert np.allclose(yy, y1[:2000], rtol=1e-6, atol=1e-6)
+    s1.close()
+    s2.close()
+
+
+def test_set_surrogate_rejects_unsupported_contexts(pkg):
+    w = pi.plain_fp64_plate(nx=8, ny=8)
+    g = pkg.Solver(w)  # FP64 element mode
+    s = pkg.pdn_sur_create(_mat(), LC)
+    with pytest.raises(pkg.PdnError) as e:
+        pkg.pdn_set_surrogate(g.ctx, s, 0.9)
+    assert e.value.code == -1
+    pkg.pdn_set_surrogate(g.ctx, None)  # back to the exact law is always allowed
+    s.close()
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def trained(pkg):
+    """A surrogate trained on 300k paths for 10,000 Adam steps (about 1.5 s)."""
+    s = pkg.pdn_sur_create(_mat(), LC, seed=1)
+    n = pkg.pdn_sur_generate(s, 300_000, 8, 0.01, 0.4, 0.9, seed=11)
+    loss = pkg.pdn_sur_train(s, 10_000, 8192, 2e-3, seed=3)
+    yield s, n, loss
+    s.close()
+
+
+def test_training_fits_held_out_points(pkg, trained):
+    """Held-out points of other paths (another seed): stress within a few
+    percent of the exact law (RMS, relative to each component's RMS), the
+    thresholds (unchanged in the regime) within 0.1."""
+    s, n, loss = trained
+    assert n > 1_000_000
+    assert loss[-1] < loss[0] / 300.0
+    h = pkg.pdn_sur_create(_mat(), LC, seed=0)
+    nh = pkg.pdn_sur_generate(h, 5000, 8, 0.01, 0.4, 0.9, seed=99)
+    x, y = pkg.pdn_sur_get_data(h, 0, nh)
+    h.close()
+    yp = pkg.pdn_sur_forward(s, x)
+    rms = np.sqrt(np.mean(y[:, :6].astype(np.float64) ** 2, axis=0))
+    rel = np.sqrt(np.mean((yp[:, :6] - y[:, :6]).astype(np.float64) ** 2, axis=0)) / rms
+    assert (rel < 0.04).all(), rel
+    assert np.max(np.abs(yp[:, 6:] - y[:, 6:])) < 0.1
+
+
+def test_impact_with_learned_law(pkg, trained):
+    """The reduced damage plate of the FP32 parity test with the learned law
+    where it applies: the peak contact force stays within 0.5 % of the exact
+    law's, and the run can return to the exact law."""
+    s, _, _ = trained
+    w = pi.damage_fp32_plate(nx=32, ny=48, Lx=25.0, Ly=37.5, H=4.4, mass=5.5e-3 / 16, steps=3000)
+    ge = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+    ge.step(3000)
+    gl = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+    pkg.pdn_set_surrogate(gl.ctx, s, 0.9)
+    gl.step(2000)
+    pkg.pdn_set_surrogate(gl.ctx, None)
+    gl.step(1000)
+    fe, fl = ge.force_history(), gl.force_history()
+    assert fe.max() > 0.0
+    assert abs(fl.max() - fe.max()) <= 5e-3 * fe.max()
+    de = ge.state()[0]
+    dl = gl.state()[0]
+    assert np.abs(dl - de).max() <= 5e-2 * np.abs(de).max()
+    ge.close()
+    gl.close()
