@@ -63,6 +63,12 @@ def hex_alg_bytes(n_hex: int, n_nodes: int) -> int:
     return n_hex * (32 + 1 + 448) + n_nodes * 24
 
 
+def coh_alg_bytes(n_coh: int) -> int:
+    """Algorithmic bytes of the interface elements of one pass: connectivity
+    (32 B) and the four thresholds read and written (2 x 16 B)."""
+    return n_coh * (32 + 2 * 4 * 4)
+
+
 def step_alg_bytes(n_hex, n_coh, n_nodes, n_surf) -> int:
     """Algorithmic bytes of one whole step (every datum moved once):
     hexes as above; interface elements connectivity + 4 thresholds read and
@@ -259,7 +265,8 @@ def run_gpu(args, ws, rank, local):
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    kernels_per_pass = 5 if plate.n_coh > 0 else 4  # contact, hex, coh, gather, tail
+    mixed = info["hex_variant"] >= 4  # one kernel for hexes and interface elements
+    kernels_per_pass = 5 if (plate.n_coh > 0 and not mixed) else 4  # contact, hex, [coh], gather, tail
     gpu_launches = (K + repeats) * kernels_per_pass + 1  # + the target/mode kernel of the call
     value = ws * plate.n_hex * K / (ms * 1e-3)
 
@@ -269,6 +276,11 @@ def run_gpu(args, ws, rank, local):
     hex_ms = prof["hex"][0]
     peak_gbs, peak_kind = measured_peaks()
     alg = hex_alg_bytes(plate.n_hex, plate.n_nodes)
+    kname = "k_hex<float>"
+    if mixed:
+        # the mixed kernel's window covers both element kinds
+        alg += coh_alg_bytes(plate.n_coh)
+        kname = "k_elem<float> (hex + interface)"
     achieved = alg / (hex_ms * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "hex_dram_traffic.json")
@@ -316,10 +328,10 @@ def run_gpu(args, ws, rank, local):
             "parallelism": f"replicas x{ws}",
         },
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                     "frac": achieved / peak_gbs, "traffic": traffic, "kernel": "k_hex<float>",
+                     "frac": achieved / peak_gbs, "traffic": traffic if not mixed else None, "kernel": kname,
                      "alg_bytes_per_launch": alg, "launch_ms": hex_ms, "peak_kind": peak_kind},
         "kernel_ms": {k: v[0] for k, v in prof.items()},
-        "autotune": {"hex_variant": info["hex_variant"], "hex_ms_per_variant": info["tune_ms"]},
+        "autotune": {"element_variant": info["hex_variant"], "force_pass_ms_per_variant": info["tune_ms"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
                 "seconds": t_e2e},
         "gpu_launches": gpu_launches,

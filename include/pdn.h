@@ -159,12 +159,15 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int32_t status;          /* sticky device status (PDN_OK or an error code) */
   int32_t precision;
-  int32_t hex_variant;     /* hex-kernel launch variant chosen by the autotuner
-                              (occupancy target 4, 5, 6 or 3 blocks/SM for 0..3);
-                              the environment variable PDN_HEX_VARIANT=0..3 fixes
-                              it instead (no timing, tune_ms stays 0) */
+  int32_t hex_variant;     /* element-kernel launch variant chosen by the autotuner:
+                              0..3 hex kernel (interface kernel on a forked stream)
+                              with an occupancy target of 4, 5, 6 or 3 blocks/SM;
+                              4..7 one mixed hex + interface kernel with the same
+                              targets.  The environment variable PDN_HEX_VARIANT
+                              (one digit) fixes it instead (no timing, tune_ms 0) */
   int32_t reserved;
-  double tune_ms[4];       /* mean hex-kernel time of each variant when tuned (0 if not) */
+  double tune_ms[8];       /* mean time of an internal-force pass with each variant when
+                              tuned (0 if not) */
 } pdn_info;
 
 /* Create a context on the current CUDA device: validate and copy the mesh,

@@ -880,106 +880,115 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
 // the tail's job); a non-finite acceleration raises the pass's flag in the
 // control block.
 //
-// gather_node: node j (< nn), given the sum of its element forces in CSR order.
-template <typename T>
-__device__ __forceinline__ void gather_node(const Dev<T> &D, int64_t j, int mode, T fx, T fy, T fz) {
-  using V4 = typename Vec4T<T>::type;
-  Ctl *ctl = D.ctl;
-  const int64_t nn = D.nn;
-  int nonfin = 0;
-  if (mode == MODE_FORCES) {
-    D.fout[j] = (double)fx;
-    D.fout[nn + j] = (double)fy;
-    D.fout[2 * nn + j] = (double)fz;
-  } else {
-    const int cur = ctl->dpar, nxt = cur ^ 1;
-    const uint8_t fl = D.nflag[j];
-    double a[3];
-    bool done = false;
-    if ((fl & 8) && mode != MODE_PRIME) {
-      const int64_t s = D.surf_of[j];
-      const int spar = (int)((ctl->step + 1) & 1);
-      if (D.act[spar][s]) {
-        const int64_t ns = D.ns;
-        const double m = D.mass[j];
-        const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
-        const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy,
-                              m * D.grav[2] - (double)fz};
-        const StrikerStep *ss = D.imp_step;
-        const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
-        const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
-        const double lam = m * adot - fdot;
-        D.lam[s] = lam;
-        if (lam < 0.0) {
-          D.rel[s] = 1;
-          a[0] = fr[0] / m;
-          a[1] = fr[1] / m;
-          a[2] = fr[2] / m;
-        } else {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
-        }
-        done = true;
-      }
-    }
-    if (!done) {
-      // free node: acceleration in the element precision, checked before
-      // widening (the element force is already rounded to T)
-      const T im = D.inv_mass[j];
-      const T ax = D.grav_t[0] - fx * im, ay = D.grav_t[1] - fy * im, az = D.grav_t[2] - fz * im;
-      if (!xfinite(ax) || !xfinite(ay) || !xfinite(az)) nonfin = 1;
-      a[0] = to_f64(ax);
-      a[1] = to_f64(ay);
-      a[2] = to_f64(az);
-    } else if (!xfinite(a[0]) || !xfinite(a[1]) || !xfinite(a[2])) {
-      nonfin = 1;
-    }
-    const double dt = D.dt;
-    const double *dc = D.d[cur];
-    const double *vc = D.v[cur];
-    double *dn = D.d[nxt];
-    double *vn = D.v[nxt];
-    double dd[3];
-    const bool phi1 = (D.phi == 1.0);
-    const double pdt2 = D.phi * dt * dt;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
-      const double vi = vc[i * nn + j];
-      const double di = dc[i * nn + j];
-      const double v1 = vi + dt * ai;
-      const double d1 = phi1 ? di + dt * v1 : di + dt * vi + pdt2 * ai;
-      vn[i * nn + j] = v1;
-      dn[i * nn + j] = d1;
-      dd[i] = d1;
-    }
-    V4 u;
-    u.x = to_elem(dd[0], T(0));
-    u.y = to_elem(dd[1], T(0));
-    u.z = to_elem(dd[2], T(0));
-    u.w = T(0);
-    D.u4[nxt][j] = u;
-  }
-  if (nonfin) atomicOr(&ctl->nonfinite, 1);
-}
-
-// One node, its element forces read straight from global memory.  The
-// node's forces are contiguous (written at their CSR positions) and summed in
-// CSR order: hexes, then interfaces, ascending.
+// One node.  Loads are grouped so that each thread waits on two rounds of
+// memory latency: first the node's CSR range together with its state (flags,
+// inverse mass, d and v of the current buffer), then its element forces, up
+// to eight at once.  The forces are contiguous (written at their CSR
+// positions) and summed in CSR order: hexes, then interfaces, ascending.
 template <typename T>
 __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
   using V4 = typename Vec4T<T>::type;
   if (j >= D.nn) return;
-  T fx = T(0), fy = T(0), fz = T(0);
+  Ctl *ctl = D.ctl;
+  const int64_t nn = D.nn;
+  const bool stepping = mode != MODE_FORCES;
   const int r0 = D.row[j], r1 = D.row[j + 1];
-#pragma unroll 4
-  for (int r = r0; r < r1; ++r) {
-    const V4 f = D.fe[r];
-    fx += f.x;
-    fy += f.y;
-    fz += f.z;
+  int cur = 0;
+  uint8_t fl = 0;
+  T im = T(0);
+  double dc[3] = {0.0, 0.0, 0.0}, vc[3] = {0.0, 0.0, 0.0};
+  if (stepping) {
+    cur = ctl->dpar;
+    fl = D.nflag[j];
+    im = D.inv_mass[j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dc[i] = D.d[cur][i * nn + j];
+      vc[i] = D.v[cur][i * nn + j];
+    }
   }
-  gather_node(D, j, mode, fx, fy, fz);
+  T fx = T(0), fy = T(0), fz = T(0);
+  for (int rb = r0; rb < r1; rb += 8) {
+    V4 f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (rb + k < r1) f[k] = D.fe[rb + k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (rb + k < r1) {
+        fx += f[k].x;
+        fy += f[k].y;
+        fz += f[k].z;
+      }
+  }
+  if (!stepping) {
+    D.fout[j] = (double)fx;
+    D.fout[nn + j] = (double)fy;
+    D.fout[2 * nn + j] = (double)fz;
+    return;
+  }
+  int nonfin = 0;
+  const int nxt = cur ^ 1;
+  double a[3];
+  bool done = false;
+  if ((fl & 8) && mode != MODE_PRIME) {
+    const int64_t s = D.surf_of[j];
+    const int spar = (int)((ctl->step + 1) & 1);
+    if (D.act[spar][s]) {
+      const int64_t ns = D.ns;
+      const double m = D.mass[j];
+      const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
+      const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy, m * D.grav[2] - (double)fz};
+      const StrikerStep *ss = D.imp_step;
+      const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
+      const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
+      const double lam = m * adot - fdot;
+      D.lam[s] = lam;
+      if (lam < 0.0) {
+        D.rel[s] = 1;
+        a[0] = fr[0] / m;
+        a[1] = fr[1] / m;
+        a[2] = fr[2] / m;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) a[i] = (fr[i] + lam * n[i]) / m;
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    // free node: acceleration in the element precision, checked before
+    // widening (the element force is already rounded to T)
+    const T ax = D.grav_t[0] - fx * im, ay = D.grav_t[1] - fy * im, az = D.grav_t[2] - fz * im;
+    if (!xfinite(ax) || !xfinite(ay) || !xfinite(az)) nonfin = 1;
+    a[0] = to_f64(ax);
+    a[1] = to_f64(ay);
+    a[2] = to_f64(az);
+  } else if (!xfinite(a[0]) || !xfinite(a[1]) || !xfinite(a[2])) {
+    nonfin = 1;
+  }
+  const double dt = D.dt;
+  double *dn = D.d[nxt];
+  double *vn = D.v[nxt];
+  double dd[3];
+  const bool phi1 = (D.phi == 1.0);
+  const double pdt2 = D.phi * dt * dt;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
+    const double v1 = vc[i] + dt * ai;
+    const double d1 = phi1 ? dc[i] + dt * v1 : dc[i] + dt * vc[i] + pdt2 * ai;
+    vn[i * nn + j] = v1;
+    dn[i * nn + j] = d1;
+    dd[i] = d1;
+  }
+  V4 u;
+  u.x = to_elem(dd[0], T(0));
+  u.y = to_elem(dd[1], T(0));
+  u.z = to_elem(dd[2], T(0));
+  u.w = T(0);
+  D.u4[nxt][j] = u;
+  if (nonfin) atomicOr(&ctl->nonfinite, 1);
 }
 
 }  // namespace detail

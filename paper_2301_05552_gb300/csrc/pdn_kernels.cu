@@ -48,6 +48,30 @@ __global__ void __launch_bounds__(128) k_coh(Dev<T> D, Mat<T> M) {
   coh_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
+// Hex and interface elements in one launch: blocks alternate between a tile
+// of hexes and a tile of interface elements (then the remainder of the
+// larger kind), so that every SM runs both the compute-bound hex warps and
+// the latency-bound interface warps at the same time.
+template <typename T, bool BOX, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_elem(Dev<T> D, Mat<T> M, int nbh, int nbc) {
+  const int mode = D.ctl->mode;
+  if (mode >= MODE_DONE) return;
+  const int b = blockIdx.x, m = nbh < nbc ? nbh : nbc;
+  int kind, idx;
+  if (b < 2 * m) {
+    kind = b & 1;
+    idx = b >> 1;
+  } else {
+    kind = nbh > nbc ? 0 : 1;
+    idx = m + (b - 2 * m);
+  }
+  const int64_t i = (int64_t)idx * blockDim.x + threadIdx.x;
+  if (kind == 0)
+    hex_item<T, BOX>(D, M, i, mode);
+  else
+    coh_item(D, M, i, mode);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
   const int mode = D.ctl->mode;
@@ -152,8 +176,32 @@ inline int grid_of(int64_t n, int b) {
 
 }  // namespace
 
-// Hex kernel variants: occupancy targets (blocks of 128 per SM, which caps the
-// registers per thread) chosen per context by the autotuner.
+// Element kernel variants chosen per context by the autotuner: 0..3 hex
+// kernel (interface kernel on the side stream) with an occupancy target of 4,
+// 5, 6 or 3 blocks of 128 per SM (which caps the registers per thread);
+// 4..7 the same targets for the mixed hex + interface kernel.
+constexpr int kMixedVariant = 4;
+
+template <typename T, bool BOX>
+void launch_elem_box(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
+  const int nbh = grid_of(D.nh, 128), nbc = D.nc > 0 ? (int)((D.nc + 127) / 128) : 0;
+  const int g = nbh + nbc;
+  switch (D.hex_variant) {
+    case 5: k_elem<T, BOX, 5><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
+    case 6: k_elem<T, BOX, 6><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
+    case 7: k_elem<T, BOX, 3><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
+    default: k_elem<T, BOX, 4><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
+  }
+}
+
+template <typename T>
+void launch_elem(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
+  if (D.all_boxes)
+    launch_elem_box<T, true>(D, M, s);
+  else
+    launch_elem_box<T, false>(D, M, s);
+}
+
 template <typename T>
 void launch_hex(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
@@ -187,6 +235,22 @@ void launch_hex(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_t gather_block,
                         cudaEvent_t *ev, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  bool mixed = D.hex_variant >= kMixedVariant;
+  if constexpr (std::is_same<T, float>::value) mixed = mixed && D.sur_params == nullptr;
+  if (mixed) {
+    // one launch for both element kinds; the interface event pair is empty
+    if (ev) cudaEventRecord(ev[0], s);
+    k_contact<T><<<grid_of(D.ns, 256), 256, 0, s>>>(D);
+    if (ev) cudaEventRecord(ev[1], s);
+    launch_elem(D, M, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (ev) cudaEventRecord(ev[3], s);
+    k_gather<T><<<grid_of(D.nn, gather_block), gather_block, 0, s>>>(D);
+    if (ev) cudaEventRecord(ev[4], s);
+    k_tail<T><<<1, 256, 0, s>>>(D);
+    if (ev) cudaEventRecord(ev[5], s);
+    return cudaGetLastError();
+  }
   const bool concurrent = side != nullptr && ev == nullptr && D.nc > 0;
   if (ev) cudaEventRecord(ev[0], s);
   k_contact<T><<<grid_of(D.ns, 256), 256, 0, s>>>(D);
