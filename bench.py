@@ -144,6 +144,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum over the ranks of a list of local timings (the
+    job's time is its slowest replica's); identity on one process."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world_size: int, units_per_rank: float, ms: float) -> float:
+    """Units processed by all ranks (each rank one replica of the workload)
+    per second of the slowest rank's time."""
+    return world_size * units_per_rank / (ms * 1e-3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,14 +278,11 @@ def run_gpu(args, ws, rank, local):
     ms = ev0.elapsed_time(ev1)
     info = pkg.pdn_get_info(ctx)
     repeats = info["n_repeats"] - rep0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(dist, [ms], "cuda")[0]
     mixed = info["hex_variant"] >= 4  # one kernel for hexes and interface elements
     kernels_per_pass = 5 if (plate.n_coh > 0 and not mixed) else 4  # contact, hex, [coh], gather, tail
     gpu_launches = (K + repeats) * kernels_per_pass + 1  # + the target/mode kernel of the call
-    value = ws * plate.n_hex * K / (ms * 1e-3)
+    value = whole_job_rate(ws, plate.n_hex * K, ms)
 
     # per-kernel device times over a window of the same run (CUDA events on
     # the library's stream around every launch)
@@ -307,11 +321,8 @@ def run_gpu(args, ws, rank, local):
     h2d = (plate.X.nbytes + plate.hex.nbytes + plate.coh.nbytes + plate.ply_of_hex.nbytes + plate.fixed.nbytes
            + plate.surf.nbytes + plate.ply_angle_deg.nbytes)
     d2h = hist.nbytes + d_fin.nbytes + v_fin.nbytes + 24 + 80
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = ws * plate.n_hex * K / t_e2e
+    t_e2e = max_over_ranks(dist, [t_e2e], "cuda")[0]
+    e2e_value = whole_job_rate(ws, plate.n_hex * K, t_e2e * 1e3)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
@@ -410,11 +421,8 @@ def run_batch(args, ws, rank, local):
     peaks_p = np.array([pkg.pdn_contact_force(c)[1] for c in ctxs])
     for c in ctxs:
         c.close()
-    if dist is not None:
-        t = torch.tensor([ms_batch, ms_plain], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_batch, ms_plain = (float(x) for x in t.tolist())
-    value = ws * n_hex * K / (ms_batch * 1e-3)
+    ms_batch, ms_plain = max_over_ranks(dist, [ms_batch, ms_plain], "cuda")
+    value = whole_job_rate(ws, n_hex * K, ms_batch)
     alg = sum(step_alg_bytes(w.plate.n_hex, w.plate.n_coh, w.plate.n_nodes, w.plate.n_surf) for w in cases)
     peak_gbs, peak_kind = measured_peaks()
     achieved = alg * K / (ms_batch * 1e-3) / 1e9
