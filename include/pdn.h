@@ -164,10 +164,10 @@ typedef struct {
                               with an occupancy target of 4, 5, 6 or 3 blocks/SM;
                               4..7 one mixed hex + interface kernel with the same
                               targets.  The environment variable PDN_HEX_VARIANT
-                              (one digit) fixes it instead (no timing, tune_ms 0) */
+                              (0..7) fixes it instead (no timing, tune_ms 0) */
   int32_t reserved;
-  double tune_ms[8];       /* mean time of an internal-force pass with each variant when
-                              tuned (0 if not) */
+  double tune_ms[12];      /* mean time of an internal-force pass with each variant when
+                              tuned (0 if not; entries 8..11 unused) */
 } pdn_info;
 
 /* Create a context on the current CUDA device: validate and copy the mesh,

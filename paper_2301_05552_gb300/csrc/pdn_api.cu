@@ -472,7 +472,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   auto layout = [&](Arena &A) {
     P.hex = A.take<int32_t>(sizeof(int32_t) * nh * 8);
     P.coh = A.take<int32_t>(sizeof(int32_t) * nc1 * 8);
-    P.ply = A.take<int8_t>(nh);
+    P.ply = A.take<int8_t>((nh + 15) & ~int64_t(15));  // whole 16-byte words (read as words)
     P.X4 = A.take<char>(ts * 4 * nn);
     P.nflag = A.take<uint8_t>(nn);
     P.surf = A.take<int32_t>(sizeof(int32_t) * ns1);
@@ -490,7 +490,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       P.hist[b] = A.take<char>(ts * 7 * 8 * nh);
       P.rD[b] = A.take<char>(ts * 4 * nc1);
       P.act[b] = A.take<uint8_t>((ns1 + 15) & ~int64_t(15));  // read in 16-byte words by the tail
-      P.pflag[b] = A.take<uint8_t>(nh);
+      P.pflag[b] = A.take<uint8_t>((nh + 15) & ~int64_t(15));
       P.cflag[b] = A.take<uint8_t>(nc1);
     }
     P.fe = A.take<char>(ts * 4 * (nh + nc) * 8);
@@ -982,7 +982,7 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
   info->precision = ctx->precision;
   info->hex_variant = ctx->precision == PDN_FP64 ? ctx->Dd.hex_variant : ctx->Df.hex_variant;
   info->reserved = 0;
-  for (int v = 0; v < 8; ++v) info->tune_ms[v] = ctx->tune_ms[v];
+  for (int v = 0; v < 12; ++v) info->tune_ms[v] = ctx->tune_ms[v];
   return PDN_OK;
 }
 

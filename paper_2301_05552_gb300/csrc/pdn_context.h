@@ -49,7 +49,7 @@ struct pdn_ctx {
   int64_t hist_cap = 0;
   bool has_imp = false;
   bool tuned = false;
-  float tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // mean element-kernel time per variant (autotuner)
+  float tune_ms[12] = {};  // mean internal-force pass time per variant (autotuner)
   cudaGraphExec_t graph = nullptr;
   // side stream for the interface kernel, forked from and joined back into
   // the main stream inside every pass

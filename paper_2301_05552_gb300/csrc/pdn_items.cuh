@@ -133,35 +133,49 @@ __host__ __device__ constexpr int pair_point(int p, int l) {
 // gradient, the Green strain, both rotations, P = S F^T and the mode-space
 // force sums run as packed pairs; the intralaminar law runs per point.
 // Same formulation as the scalar element below (Eq. fcont, Algorithm 4).
+// The compute of hex_item_box_pairs from the element's node displacements
+// ua (by node) and the x-y-z extents of the box (corner 6 minus corner 0).
+__device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
+                                                   const float (&ua)[8][3], float ex, float ey, float ez,
+                                                   bool pristine_in, int ply, const int4 *pos2);
+
 __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode) {
   using V4 = float4;
   const Ctl *ctl = D.ctl;
   if (e >= D.nh) return;
-  const int64_t nh = D.nh;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
-  const int hb = ctl->hpar;
   const V4 *__restrict__ U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  float ua[8][3];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const V4 u = U[nd[a]];
+    ua[a][0] = u.x;
+    ua[a][1] = u.y;
+    ua[a][2] = u.z;
+  }
+  const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
+  const bool pristine_in = D.pflag[0] != nullptr && D.pflag[ctl->hpar][e] != 0;
+  hex_box_pairs_core(D, M, e, mode, ua, x6.x - x0.x, x6.y - x0.y, x6.z - x0.z, pristine_in, D.ply[e],
+                     reinterpret_cast<const int4 *>(D.pos) + 2 * e);
+}
+
+__device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
+                                                   const float (&ua)[8][3], float ex, float ey, float ez,
+                                                   bool pristine_in, int ply, const int4 *pos2) {
+  const Ctl *ctl = D.ctl;
+  const int64_t nh = D.nh;
+  const int hb = ctl->hpar;
   const float *__restrict__ hin = D.hist[hb] + e;
   float *__restrict__ hout = D.hist[hb ^ 1] + e;
-  const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][e] != 0;
   bool dirty = false;
   float bm[8][3];
   float jd[3], wd[3], vol;
   {
-    float ua[8][3];
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const V4 u = U[nd[a]];
-      ua[a][0] = u.x;
-      ua[a][1] = u.y;
-      ua[a][2] = u.z;
-    }
     to_modes(ua, bm);
-    const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
-    const float J0 = 0.5f * (x6.x - x0.x), J1 = 0.5f * (x6.y - x0.y), J2 = 0.5f * (x6.z - x0.z);
+    const float J0 = 0.5f * ex, J1 = 0.5f * ey, J2 = 0.5f * ez;
     const float det = J0 * (J1 * J2);
     jd[0] = 1.0f / J0;
     jd[1] = 1.0f / J1;
@@ -171,7 +185,6 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
     wd[2] = det * jd[2];
     vol = 8.0f * det;
   }
-  const int ply = D.ply[e];
   const float cs = M.ply_c[ply], sn = M.ply_s[ply];
   const float c2 = cs * cs, s2 = sn * sn, csn = cs * sn;
   const ElemLaw<float> L = elem_law(M, e);
@@ -311,8 +324,8 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
   float f[8][3];
   from_modes(C, f);
-  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e);
-  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e + 1);
+  const int4 p0 = pos2[0];
+  const int4 p1 = pos2[1];
   const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
   for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);

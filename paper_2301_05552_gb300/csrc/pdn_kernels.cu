@@ -13,6 +13,7 @@
 #include "pdn_internal.h"
 
 #include <cstdint>
+#include <algorithm>
 #include <type_traits>
 
 #include "pdn.h"
