@@ -444,7 +444,7 @@ def run_batch(args, ws, rank, local):
             "f_peak_max_rel_diff_vs_plain": float(np.max(np.abs(peaks_b - peaks_p) / scale)),
             "f_peak_N_range": [float(peaks_b.min()), float(peaks_b.max())],
             "step_repeats": int(repeats_b),
-            "schedule": {k: info[k] for k in ("blocks_per_sm", "tile_items", "reg_variant", "grid", "graph")},
+            "schedule": {k: info[k] for k in ("dataflow", "blocks_per_sm", "tile_items", "reg_variant", "grid", "graph")},
             "autotune_candidates": info0["candidates"],
             "passes": info["passes"] - info0["passes"], "launches": info["launches"] - info0["launches"],
         },

@@ -12,15 +12,23 @@
  *   4. the tail of every plate: its own reaction sum (a segmented reduction:
  *      one block per plate), commit / repeat (Algorithm 2) / halt, and its
  *      striker update with its own time step;
- * with a grid-wide barrier between phases.  The launch is cooperative (all
+ * Two schedules: a grid-wide barrier between phases, or dataflow (one queue
+ * of pass/phase/tile positions; a tile waits only until the previous phase of
+ * its own plate is complete, so one plate's gather overlaps another plate's
+ * elements).  Every wait is bounded in time.  The launch is cooperative (all
  * blocks resident), captured in a CUDA graph, and repeats passes until every
  * plate has reached its target step.  Each plate follows the same device
- * state machine and the same per-item arithmetic as pdn_step, so a plate
- * stepped in a batch gives the same result as the plate stepped alone.
+ * state machine and the same per-item source code as pdn_step, with the
+ * same fixed reduction orders, so a plate stepped in a batch follows the
+ * plate stepped alone to floating-point rounding (the compiler may contract
+ * multiply-adds differently in different kernel instantiations) and
+ * repeated runs of one schedule are bitwise identical.
  *
- * Tile size, blocks per SM and the kernel's register budget are chosen by an
- * autotuner on the first pdn_batch_step (timing internal-force passes, which
- * leave the state unchanged). */
+ * The schedule, tile size, blocks per SM and the kernel's register budget are
+ * chosen by an autotuner on the first pdn_batch_step (timing internal-force
+ * passes, which leave the state unchanged); the environment variable
+ * PDN_BATCH_SCHEDULE="s" or "s,r" restricts it to schedule s (0 barrier, 1
+ * dataflow) and register variant r (see pdn_batch_info.reg_variant). */
 #ifndef PDN_BATCH_H
 #define PDN_BATCH_H
 
@@ -53,6 +61,10 @@ typedef struct {
   int32_t tune_bps[16];    /* candidate: blocks per SM */
   int32_t tune_tile[16];   /* candidate: items per tile */
   int32_t tune_var[16];    /* candidate: register variant */
+  int32_t dataflow;        /* chosen schedule: 0 grid barriers between phases, 1 dataflow
+                              (per-plate phase dependencies, no barrier) */
+  int32_t pad;
+  int32_t tune_flow[16];   /* candidate: schedule */
 } pdn_batch_info;
 
 /* Create a batch of n_plates (1..4096) plates on the current device.

@@ -95,7 +95,8 @@ class BatchInfo(C.Structure):
                 ("grid", C.c_int32), ("graph", C.c_int32), ("n_candidates", C.c_int32),
                 ("n_tiles", C.c_int64 * 4), ("launches", C.c_int64), ("passes", C.c_int64),
                 ("tune_ms", C.c_double * 16), ("tune_bps", C.c_int32 * 16), ("tune_tile", C.c_int32 * 16),
-                ("tune_var", C.c_int32 * 16)]
+                ("tune_var", C.c_int32 * 16), ("dataflow", C.c_int32), ("pad", C.c_int32),
+                ("tune_flow", C.c_int32 * 16)]
 
 
 _lock = threading.Lock()
@@ -475,8 +476,8 @@ def pdn_batch_get_info(b: Batch) -> dict:
     nc = info.n_candidates
     out["n_tiles"] = list(info.n_tiles)
     out["candidates"] = [dict(ms=info.tune_ms[k], blocks_per_sm=info.tune_bps[k], tile_items=info.tune_tile[k],
-                              reg_variant=info.tune_var[k]) for k in range(nc)]
-    for k in ("tune_ms", "tune_bps", "tune_tile", "tune_var"):
+                              reg_variant=info.tune_var[k], dataflow=info.tune_flow[k]) for k in range(nc)]
+    for k in ("tune_ms", "tune_bps", "tune_tile", "tune_var", "tune_flow", "pad"):
         out.pop(k)
     return out
 

@@ -1,7 +1,8 @@
 // Batched persistent launch (include/pdn_batch.h): many independent plates
 // advanced by one cooperative kernel that loops over passes; each pass walks
 // four phases (contact, elements, gather, tails) over a work queue of tiles
-// that spans all plates, with a bounded grid barrier between phases.
+// that spans all plates, with a bounded grid barrier between phases, or in the
+// dataflow schedule with bounded per-plate dependency waits instead.
 //
 // Every tile applies the same per-item bodies as the per-pass kernels
 // (pdn_items.cuh) to one plate, with that plate's state machine (Ctl), so a
@@ -10,6 +11,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -39,9 +41,10 @@ struct BatchSync {
   uint32_t bar_gen;     // barrier generation
   uint32_t queue[kPhases];
   uint32_t live[2];     // plates still running after a pass (by pass parity)
-  int32_t error;        // 1: a barrier wait gave up
+  int32_t error;        // 1: a barrier or dependency wait gave up
   int32_t passes_done;
-  uint32_t pad[6];
+  uint32_t next;        // dataflow schedule: next queue position
+  uint32_t pad[5];
 };
 
 template <typename T>
@@ -183,15 +186,144 @@ __global__ void __launch_bounds__(kBatchBlock, MINB) k_batch(BatchArgs<T> A) {
   if (blockIdx.x == 0 && threadIdx.x == 0) sy->passes_done = pass;
 }
 
+// Dataflow schedule: one queue of (pass, phase, tile) positions, pass after
+// pass in the phase order of the tile list.  A block takes the next position
+// and waits (bounded in time) only until the previous phase of the same plate
+// is complete: every tile of it for this pass, or the plate's tail of the
+// previous pass for its contact tiles.  Completed tiles are counted per plate
+// and phase.  Dependencies always sit earlier in the queue and every block is
+// resident (cooperative launch), so the earliest unfinished tile can always
+// run.  Phases of different plates overlap (one plate's gather with another
+// plate's elements) instead of draining the GPU at a barrier.
+template <typename T>
+struct FlowArgs {
+  const Dev<T> *D;
+  const Mat<T> *M;
+  const int4 *tiles;     // one pass: (plate, kind, begin, end), phase after phase
+  const int4 *ntiles;    // [n_plates]: tiles of the contact, element and gather phases, 1 tail
+  uint32_t *done;        // [n_plates][4] completed tiles in this launch
+  int32_t *live;         // plates not yet done or halted
+  BatchSync *sync;
+  int32_t tiles_per_pass;
+  int32_t passes;
+  int64_t timeout_ns;
+};
+
+__device__ __forceinline__ int phase_of(int kind) {
+  return kind == TK_CONTACT ? 0 : (kind == TK_GATHER ? 2 : (kind == TK_TAIL ? 3 : 1));
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kBatchBlock, MINB) k_batch_flow(FlowArgs<T> A) {
+  __shared__ Dev<T> sD;
+  __shared__ Mat<T> sM;
+  __shared__ int64_t s_g;
+  __shared__ int s_go;
+  BatchSync *sy = A.sync;
+  const int64_t total = (int64_t)A.passes * A.tiles_per_pass;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0)
+      s_g = (*(volatile int32_t *)A.live <= 0 || *(volatile int32_t *)&sy->error) ? total
+                                                                                 : (int64_t)atomicAdd(&sy->next, 1u);
+    __syncthreads();
+    const int64_t g = s_g;
+    if (g >= total) break;  // uniform over the block
+    const int pass = (int)(g / A.tiles_per_pass);
+    const int4 tl = A.tiles[g % A.tiles_per_pass];
+    const int P = tl.x, ph = phase_of(tl.y);
+    if (threadIdx.x == 0) {
+      int go = 1;
+      const Ctl *ctl = A.D[P].ctl;
+      if (*(volatile const int32_t *)&ctl->mode < MODE_DONE) {
+        const int4 nt = A.ntiles[P];
+        int dep;
+        uint32_t need;
+        if (ph == 0 || (ph == 1 && nt.x == 0)) {
+          dep = 3;  // the plate's tail of the previous pass
+          need = (uint32_t)pass;
+        } else {
+          dep = ph - 1;
+          need = (uint32_t)(pass + 1) * (uint32_t)(dep == 0 ? nt.x : (dep == 1 ? nt.y : nt.z));
+        }
+        volatile uint32_t *cnt = &A.done[P * 4 + dep];
+        if (*cnt < need) {
+          const uint64_t t0 = global_ns();
+          while (*cnt < need) {
+            if (*(volatile int32_t *)&sy->error) {
+              go = 0;
+              break;
+            }
+            if ((int64_t)(global_ns() - t0) > A.timeout_ns) {
+              atomicExch(&sy->error, 1);
+              go = 0;
+              break;
+            }
+            __nanosleep(64);
+          }
+        }
+        __threadfence();
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) return;
+    if (P != cur) {
+      copy_words(&sD, &A.D[P]);
+      copy_words(&sM, &A.M[P]);
+      cur = P;
+    }
+    __syncthreads();
+    const int mode = *(volatile const int32_t *)&sD.ctl->mode;
+    switch (tl.y) {
+      case TK_CONTACT:
+        if (mode == MODE_ADVANCE || mode == MODE_REPEAT)
+          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) contact_item(sD, i, mode);
+        break;
+      case TK_HEX:
+        if (mode < MODE_DONE) {
+          if (sD.all_boxes)
+            for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) hex_item<T, true>(sD, sM, i, mode);
+          else
+            for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) hex_item<T, false>(sD, sM, i, mode);
+        }
+        break;
+      case TK_COH:
+        if (mode < MODE_DONE)
+          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) coh_item(sD, sM, i, mode);
+        break;
+      case TK_GATHER:
+        if (mode < MODE_DONE)
+          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) gather_item(sD, i, mode);
+        break;
+      default:  // TK_TAIL
+        if (mode < MODE_DONE) {
+          tail_block(sD, mode);
+          if (threadIdx.x == 0) {
+            atomicMax(&sy->passes_done, pass + 1);
+            if (*(volatile const int32_t *)&sD.ctl->mode >= MODE_DONE) atomicSub(A.live, 1);
+          }
+        }
+        break;
+    }
+    __syncthreads();  // every item of the tile is issued before it counts as done
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(&A.done[P * 4 + ph], 1u);
+    }
+  }
+}
+
 // Mode and target of every plate (plates that halted keep their state).
 template <typename T>
-__global__ void k_batch_set_mode(const Dev<T> *D, int n, int32_t mode, int64_t nsteps) {
+__global__ void k_batch_set_mode(const Dev<T> *D, int n, int32_t mode, int64_t nsteps, int32_t *live) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   Ctl *c = D[p].ctl;
   if (c->mode == MODE_HALT) return;
   c->mode = mode;
   c->target = c->step + nsteps;
+  if (mode < MODE_DONE) atomicAdd(live, 1);
 }
 
 // Every plate's control block and the launch's sync words, for one copy.
@@ -222,17 +354,21 @@ struct pdn_batch {
   int4 *d_tiles = nullptr;
   size_t tiles_cap = 0;
   BatchSync *d_sync = nullptr;
+  uint32_t *d_done = nullptr;  // dataflow: completed tiles per plate and phase [n][4]
+  int32_t *d_live = nullptr;   // plates not yet done or halted
+  int4 *d_ntiles = nullptr;    // tiles per plate of the contact, element, gather phases, 1 tail
   Ctl *d_ctl_all = nullptr;    // [n] followed by a BatchSync copy
   unsigned char *h_buf = nullptr;  // pinned copy of the same
   int32_t tile_off[kPhases + 1] = {0, 0, 0, 0, 0};
   // schedule
   int var = 0, bps = 0, tile_items = 256, grid = 0;
+  int flow = 0;  // 0: grid barriers between phases, 1: dataflow dependencies
   bool tuned = false;
   cudaGraphExec_t graph = nullptr;
   bool graph_ok = false;
   int n_cand = 0;
   double tune_ms[kMaxCand] = {};
-  int32_t tune_bps[kMaxCand] = {}, tune_tile[kMaxCand] = {}, tune_var[kMaxCand] = {};
+  int32_t tune_bps[kMaxCand] = {}, tune_tile[kMaxCand] = {}, tune_var[kMaxCand] = {}, tune_flow[kMaxCand] = {};
   int64_t launches = 0, passes = 0;
   int status = PDN_OK;
   std::string err;
@@ -264,12 +400,15 @@ const void *kernel_of() {
 }
 
 template <typename T>
-const void *kernel_for(int var) {
+const void *kernel_for(int flow, int var) {
+  if (flow)
+    return var == 0 ? reinterpret_cast<const void *>(&k_batch_flow<T, 4>)
+                    : reinterpret_cast<const void *>(&k_batch_flow<T, 1>);
   return var == 0 ? kernel_of<T, 4>() : kernel_of<T, 1>();
 }
 
-const void *kernel_ptr(const pdn_batch *b, int var) {
-  return b->precision == PDN_FP64 ? kernel_for<double>(var) : kernel_for<float>(var);
+const void *kernel_ptr(const pdn_batch *b, int flow, int var) {
+  return b->precision == PDN_FP64 ? kernel_for<double>(flow, var) : kernel_for<float>(flow, var);
 }
 
 // Tiles of every phase for a tile size; heavier element tiles (hexes) are
@@ -290,6 +429,13 @@ int build_tiles(pdn_batch *b, int tile_items) {
   b->tile_off[3] = (int32_t)t.size();
   for (int p = 0; p < b->n; ++p) t.push_back(make_int4(p, TK_TAIL, 0, 0));
   b->tile_off[4] = (int32_t)t.size();
+  std::vector<int4> nt(b->n);
+  for (int p = 0; p < b->n; ++p) {
+    auto tiles = [&](int64_t n) { return (int)((n + tile_items - 1) / tile_items); };
+    const pdn_ctx *c = b->plates[p];
+    nt[p] = make_int4(tiles(c->ns), tiles(c->nh) + tiles(c->nc), tiles(c->nn), 1);
+  }
+  PB_CU(cudaMemcpy(b->d_ntiles, nt.data(), sizeof(int4) * b->n, cudaMemcpyHostToDevice), "upload tile counts");
   if (t.size() > b->tiles_cap) {
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
@@ -319,7 +465,24 @@ BatchArgs<T> args_of(pdn_batch *b, int passes, int stall_block, int64_t timeout_
 constexpr int64_t kBarrierTimeoutNs = 2000000000LL;  // 2 s: far beyond any phase of a pass
 
 // One persistent launch (cooperative) of the chosen schedule.
-cudaError_t launch_batch(pdn_batch *b, int var, int grid, int passes, int stall_block, int64_t timeout_ns) {
+template <typename T>
+FlowArgs<T> flow_args_of(pdn_batch *b, int passes, int64_t timeout_ns) {
+  FlowArgs<T> A{};
+  A.D = reinterpret_cast<const Dev<T> *>(b->d_dev);
+  A.M = reinterpret_cast<const Mat<T> *>(b->d_mat);
+  A.tiles = b->d_tiles;
+  A.ntiles = b->d_ntiles;
+  A.done = b->d_done;
+  A.live = b->d_live;
+  A.sync = b->d_sync;
+  A.tiles_per_pass = b->tile_off[kPhases];
+  A.passes = passes;
+  A.timeout_ns = timeout_ns;
+  return A;
+}
+
+cudaError_t launch_batch(pdn_batch *b, int flow, int var, int grid, int passes, int stall_block,
+                         int64_t timeout_ns) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kBatchBlock);
@@ -332,6 +495,18 @@ cudaError_t launch_batch(pdn_batch *b, int var, int grid, int passes, int stall_
   cfg.numAttrs = 1;
   cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
   if (e != cudaSuccess) return e;
+  if (flow) {
+    e = cudaMemsetAsync(b->d_done, 0, sizeof(uint32_t) * 4 * (size_t)b->n, b->stream);
+    if (e != cudaSuccess) return e;
+    if (b->precision == PDN_FP64) {
+      FlowArgs<double> A = flow_args_of<double>(b, passes, timeout_ns);
+      return var == 0 ? cudaLaunchKernelEx(&cfg, k_batch_flow<double, 4>, A)
+                      : cudaLaunchKernelEx(&cfg, k_batch_flow<double, 1>, A);
+    }
+    FlowArgs<float> A = flow_args_of<float>(b, passes, timeout_ns);
+    return var == 0 ? cudaLaunchKernelEx(&cfg, k_batch_flow<float, 4>, A)
+                    : cudaLaunchKernelEx(&cfg, k_batch_flow<float, 1>, A);
+  }
   if (b->precision == PDN_FP64) {
     BatchArgs<double> A = args_of<double>(b, passes, stall_block, timeout_ns);
     return var == 0 ? cudaLaunchKernelEx(&cfg, k_batch<double, 4>, A) : cudaLaunchKernelEx(&cfg, k_batch<double, 1>, A);
@@ -342,10 +517,13 @@ cudaError_t launch_batch(pdn_batch *b, int var, int grid, int passes, int stall_
 
 int set_modes(pdn_batch *b, int32_t mode, int64_t nsteps) {
   const int g = (b->n + 127) / 128;
+  PB_CU(cudaMemsetAsync(b->d_live, 0, sizeof(int32_t), b->stream), "live plates");
   if (b->precision == PDN_FP64)
-    k_batch_set_mode<double><<<g, 128, 0, b->stream>>>(reinterpret_cast<const Dev<double> *>(b->d_dev), b->n, mode, nsteps);
+    k_batch_set_mode<double><<<g, 128, 0, b->stream>>>(reinterpret_cast<const Dev<double> *>(b->d_dev), b->n, mode,
+                                                       nsteps, b->d_live);
   else
-    k_batch_set_mode<float><<<g, 128, 0, b->stream>>>(reinterpret_cast<const Dev<float> *>(b->d_dev), b->n, mode, nsteps);
+    k_batch_set_mode<float><<<g, 128, 0, b->stream>>>(reinterpret_cast<const Dev<float> *>(b->d_dev), b->n, mode,
+                                                      nsteps, b->d_live);
   PB_CU(cudaGetLastError(), "set modes");
   return PDN_OK;
 }
@@ -369,9 +547,10 @@ int collect(pdn_batch *b) {
 }
 
 // Resident blocks per SM of a kernel variant (the cooperative limit).
-int max_bps(pdn_batch *b, int var) {
+int max_bps(pdn_batch *b, int flow, int var) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_ptr(b, var), kBatchBlock, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_ptr(b, flow, var), kBatchBlock, 0) != cudaSuccess)
+    return 0;
   return nb;
 }
 
@@ -380,18 +559,28 @@ int max_bps(pdn_batch *b, int var) {
 int autotune(pdn_batch *b) {
   if (b->tuned) return PDN_OK;
   struct Cand {
-    int var, bps, tile;
+    int flow, var, bps, tile;
   };
   std::vector<Cand> cands;
-  const int tiles[2] = {128, 512};
-  for (int var = 0; var < 2; ++var) {
-    const int lim = max_bps(b, var);
-    for (int bps = std::min(lim, 4); bps >= 1; --bps) {
-      if (var == 0 && bps < 2) continue;
-      if (var == 1 && bps > 2) continue;
-      for (int ti : tiles) cands.push_back({var, bps, ti});
+  const int tiles[2] = {512, 2048};
+  // PDN_BATCH_SCHEDULE="s" or "s,r" restricts the candidates to schedule s
+  // (0 barrier, 1 dataflow) and register variant r
+  int flow0 = 0, flow1 = 1, var0 = 0, var1 = 1;
+  if (const char *fs = std::getenv("PDN_BATCH_SCHEDULE")) {
+    if (fs[0] == '0' || fs[0] == '1') {
+      flow0 = flow1 = fs[0] - '0';
+      if (fs[1] == ',' && (fs[2] == '0' || fs[2] == '1')) var0 = var1 = fs[2] - '0';
     }
   }
+  for (int flow = flow0; flow <= flow1; ++flow)
+    for (int var = var0; var <= var1; ++var) {
+      const int lim = max_bps(b, flow, var);
+      for (int bps = std::min(lim, 4); bps >= 1; --bps) {
+        if (var == 0 && bps < 3) continue;  // the 128-register kernel: 4 or 3 blocks per SM
+        if (var == 1 && bps != 2) continue;  // the 240-register kernel: 2 blocks per SM
+        for (int ti : tiles) cands.push_back({flow, var, bps, ti});
+      }
+    }
   if (cands.empty()) return bfail(b, PDN_E_CUDA, "no resident block fits the batch kernel");
   if ((int)cands.size() > kMaxCand) cands.resize(kMaxCand);
   cudaEvent_t e0, e1;
@@ -410,7 +599,7 @@ int autotune(pdn_batch *b) {
       rc = set_modes(b, MODE_FORCES, 0);
       if (rc) return rc;
       PB_CU(cudaEventRecord(e0, b->stream), "tune record");
-      PB_CU(launch_batch(b, c.var, grid, 1, -1, kBarrierTimeoutNs), "tune launch");
+      PB_CU(launch_batch(b, c.flow, c.var, grid, 1, -1, kBarrierTimeoutNs), "tune launch");
       PB_CU(cudaEventRecord(e1, b->stream), "tune record");
       rc = collect(b);
       if (rc) return rc;
@@ -428,6 +617,7 @@ int autotune(pdn_batch *b) {
     b->tune_bps[k] = c.bps;
     b->tune_tile[k] = c.tile;
     b->tune_var[k] = c.var;
+    b->tune_flow[k] = c.flow;
     if (ms < best) {
       best = ms;
       pick = c;
@@ -438,6 +628,7 @@ int autotune(pdn_batch *b) {
   int rc = build_tiles(b, pick.tile);
   if (rc) return rc;
   b->var = pick.var;
+  b->flow = pick.flow;
   b->bps = pick.bps;
   b->grid = pick.bps * b->sms;
   b->tuned = true;
@@ -445,7 +636,7 @@ int autotune(pdn_batch *b) {
   cudaGraph_t g = nullptr;
   b->graph_ok = false;
   if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    cudaError_t e = launch_batch(b, b->var, b->grid, kBatchPasses, -1, kBarrierTimeoutNs);
+    cudaError_t e = launch_batch(b, b->flow, b->var, b->grid, kBatchPasses, -1, kBarrierTimeoutNs);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&b->graph, g, 0) == cudaSuccess)
       b->graph_ok = true;
@@ -520,6 +711,9 @@ void pdn_batch_destroy(pdn_batch *b) {
   if (b->d_mat) cudaFree(b->d_mat);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_sync) cudaFree(b->d_sync);
+  if (b->d_done) cudaFree(b->d_done);
+  if (b->d_live) cudaFree(b->d_live);
+  if (b->d_ntiles) cudaFree(b->d_ntiles);
   if (b->d_ctl_all) cudaFree(b->d_ctl_all);
   if (b->h_buf) cudaFreeHost(b->h_buf);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -572,6 +766,9 @@ int pdn_batch_init(pdn_batch **out, int32_t n_plates, const pdn_mesh_desc *meshe
   int rc = b->precision == PDN_FP64 ? upload_records<double>(b) : upload_records<float>(b);
   if (rc) return fail_init(rc, b->err);
   if (cudaMalloc(&b->d_sync, sizeof(BatchSync)) != cudaSuccess ||
+      cudaMalloc(&b->d_done, sizeof(uint32_t) * 4 * (size_t)n_plates) != cudaSuccess ||
+      cudaMalloc(&b->d_live, sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&b->d_ntiles, sizeof(int4) * (size_t)n_plates) != cudaSuccess ||
       cudaMalloc(&b->d_ctl_all, sizeof(Ctl) * (size_t)n_plates + sizeof(BatchSync)) != cudaSuccess ||
       cudaMallocHost(&b->h_buf, sizeof(Ctl) * (size_t)n_plates + sizeof(BatchSync)) != cudaSuccess)
     return fail_init(PDN_E_OOM, "batch control buffers");
@@ -609,7 +806,7 @@ int pdn_batch_step(pdn_batch *b, int64_t nsteps) {
   const int64_t guard_max = (nsteps * (int64_t)(max_rep + 1)) / kBatchPasses + 4;
   for (int64_t guard = 0;; ++guard) {
     cudaError_t e = b->graph_ok ? cudaGraphLaunch(b->graph, b->stream)
-                                : launch_batch(b, b->var, b->grid, kBatchPasses, -1, kBarrierTimeoutNs);
+                                : launch_batch(b, b->flow, b->var, b->grid, kBatchPasses, -1, kBarrierTimeoutNs);
     if (e != cudaSuccess) return bcuda(b, e, "batch launch");
     ++b->launches;
     rc = collect(b);
@@ -618,7 +815,7 @@ int pdn_batch_step(pdn_batch *b, int64_t nsteps) {
     b->passes += sy.passes_done;
     if (sy.error) {
       b->status = PDN_E_TIMEOUT;
-      return bfail(b, PDN_E_TIMEOUT, "a grid barrier wait gave up (bounded wait)");
+      return bfail(b, PDN_E_TIMEOUT, "a grid barrier or dependency wait gave up (bounded wait)");
     }
     bool done = true;
     for (int p = 0; p < b->n; ++p) {
@@ -648,7 +845,9 @@ int pdn_batch_get_info(pdn_batch *b, pdn_batch_info *info) {
   for (int k = 0; k < kPhases; ++k) info->n_tiles[k] = b->tile_off[k + 1] - b->tile_off[k];
   info->launches = b->launches;
   info->passes = b->passes;
+  info->dataflow = b->flow;
   for (int k = 0; k < b->n_cand && k < 16; ++k) {
+    info->tune_flow[k] = b->tune_flow[k];
     info->tune_ms[k] = b->tune_ms[k];
     info->tune_bps[k] = b->tune_bps[k];
     info->tune_tile[k] = b->tune_tile[k];
@@ -672,10 +871,10 @@ int pdn_batch_test_barrier_timeout(pdn_batch *b, double timeout_ms) {
     if (rc) return rc;
   }
   const int var = b->tuned ? b->var : 0;
-  const int bps = std::max(1, std::min(2, max_bps(b, var)));
+  const int bps = std::max(1, std::min(2, max_bps(b, 0, var)));
   const int grid = b->tuned ? b->grid : bps * b->sms;
   if (grid < 2) return bfail(b, PDN_E_STATE, "the test needs at least two blocks");
-  cudaError_t e = launch_batch(b, var, grid, 1, 0, (int64_t)(timeout_ms * 1e6));
+  cudaError_t e = launch_batch(b, 0, var, grid, 1, 0, (int64_t)(timeout_ms * 1e6));
   if (e != cudaSuccess) return bcuda(b, e, "test launch");
   rc = collect(b);
   if (rc) return rc;
