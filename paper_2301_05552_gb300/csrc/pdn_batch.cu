@@ -562,10 +562,10 @@ int autotune(pdn_batch *b) {
     int flow, var, bps, tile;
   };
   std::vector<Cand> cands;
-  const int tiles[2] = {512, 2048};
+  const int tiles[3] = {1024, 2048, 4096};
   // PDN_BATCH_SCHEDULE="s" or "s,r" restricts the candidates to schedule s
-  // (0 barrier, 1 dataflow) and register variant r
-  int flow0 = 0, flow1 = 1, var0 = 0, var1 = 1;
+  // (0 barrier, 1 dataflow) and selects register variant r (default 0)
+  int flow0 = 0, flow1 = 1, var0 = 0, var1 = 0;  // the 240-register variant only on request
   if (const char *fs = std::getenv("PDN_BATCH_SCHEDULE")) {
     if (fs[0] == '0' || fs[0] == '1') {
       flow0 = flow1 = fs[0] - '0';
