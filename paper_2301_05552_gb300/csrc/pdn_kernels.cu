@@ -13,6 +13,7 @@
 #include "pdn_internal.h"
 
 #include <cstdint>
+#include <cstdlib>
 #include <algorithm>
 #include <type_traits>
 
@@ -25,11 +26,22 @@ namespace {
 
 using namespace detail;
 
+// Programmatic dependent launch: the next kernel of the pass may be
+// scheduled once every block of this one has started (its blocks then take
+// SM slots as this kernel's last wave drains), and every kernel waits for the
+// previous grid's completion before it reads anything.  Without the launch
+// attribute both instructions have no effect.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Kernels of a pass (one launch per step part); the per-item bodies are in
 // pdn_items.cuh, shared with the batched persistent kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) k_contact(Dev<T> D) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode != MODE_ADVANCE && mode != MODE_REPEAT) return;
   contact_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
@@ -37,6 +49,7 @@ __global__ void __launch_bounds__(256) k_contact(Dev<T> D) {
 
 template <typename T, bool BOX, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_hex(Dev<T> D, Mat<T> M) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   hex_item<T, BOX>(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
@@ -44,6 +57,7 @@ __global__ void __launch_bounds__(128, MINB) k_hex(Dev<T> D, Mat<T> M) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_coh(Dev<T> D, Mat<T> M) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   coh_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
@@ -55,6 +69,7 @@ __global__ void __launch_bounds__(128) k_coh(Dev<T> D, Mat<T> M) {
 // the latency-bound interface warps at the same time.
 template <typename T, bool BOX, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_elem(Dev<T> D, Mat<T> M, int nbh, int nbc) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   const int b = blockIdx.x, m = nbh < nbc ? nbh : nbc;
@@ -75,6 +90,7 @@ __global__ void __launch_bounds__(128, MINB) k_elem(Dev<T> D, Mat<T> M, int nbh,
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   gather_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
@@ -84,6 +100,7 @@ __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
 // gather, whose occupancy depends on a low register count).
 template <typename T>
 __global__ void __launch_bounds__(256) k_tail(Dev<T> D) {
+  pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   tail_block(D, mode);
@@ -170,6 +187,31 @@ __global__ void k_damage_field(Dev<T> D, Mat<T> M, int which, float *out) {
   out[e] = (float)m;
 }
 
+// Launch on the pass's main stream, with the programmatic-dependency
+// attribute unless PDN_PDL=0.
+bool pdl_on() {
+  static const bool on = [] {
+    const char *e = std::getenv("PDN_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+void launch_k(void (*k)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_on() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 inline int grid_of(int64_t n, int b) {
   int64_t g = (n + b - 1) / b;
   return (int)(g < 1 ? 1 : g);
@@ -188,10 +230,10 @@ void launch_elem_box(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
   const int nbh = grid_of(D.nh, 128), nbc = D.nc > 0 ? (int)((D.nc + 127) / 128) : 0;
   const int g = nbh + nbc;
   switch (D.hex_variant) {
-    case 5: k_elem<T, BOX, 5><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
-    case 6: k_elem<T, BOX, 6><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
-    case 7: k_elem<T, BOX, 3><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
-    default: k_elem<T, BOX, 4><<<g, 128, 0, s>>>(D, M, nbh, nbc); break;
+    case 5: launch_k(k_elem<T, BOX, 5>, g, 128, s, D, M, nbh, nbc); break;
+    case 6: launch_k(k_elem<T, BOX, 6>, g, 128, s, D, M, nbh, nbc); break;
+    case 7: launch_k(k_elem<T, BOX, 3>, g, 128, s, D, M, nbh, nbc); break;
+    default: launch_k(k_elem<T, BOX, 4>, g, 128, s, D, M, nbh, nbc); break;
   }
 }
 
@@ -214,17 +256,17 @@ void launch_hex(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
   const int g = grid_of(D.nh, 128);
   if (D.all_boxes) {
     switch (D.hex_variant) {
-      case 1: k_hex<T, true, 5><<<g, 128, 0, s>>>(D, M); break;
-      case 2: k_hex<T, true, 6><<<g, 128, 0, s>>>(D, M); break;
-      case 3: k_hex<T, true, 3><<<g, 128, 0, s>>>(D, M); break;
-      default: k_hex<T, true, 4><<<g, 128, 0, s>>>(D, M); break;
+      case 1: launch_k(k_hex<T, true, 5>, g, 128, s, D, M); break;
+      case 2: launch_k(k_hex<T, true, 6>, g, 128, s, D, M); break;
+      case 3: launch_k(k_hex<T, true, 3>, g, 128, s, D, M); break;
+      default: launch_k(k_hex<T, true, 4>, g, 128, s, D, M); break;
     }
   } else {
     switch (D.hex_variant) {
-      case 1: k_hex<T, false, 5><<<g, 128, 0, s>>>(D, M); break;
-      case 2: k_hex<T, false, 6><<<g, 128, 0, s>>>(D, M); break;
-      case 3: k_hex<T, false, 3><<<g, 128, 0, s>>>(D, M); break;
-      default: k_hex<T, false, 4><<<g, 128, 0, s>>>(D, M); break;
+      case 1: launch_k(k_hex<T, false, 5>, g, 128, s, D, M); break;
+      case 2: launch_k(k_hex<T, false, 6>, g, 128, s, D, M); break;
+      case 3: launch_k(k_hex<T, false, 3>, g, 128, s, D, M); break;
+      default: launch_k(k_hex<T, false, 4>, g, 128, s, D, M); break;
     }
   }
 }
@@ -241,20 +283,20 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
   if (mixed) {
     // one launch for both element kinds; the interface event pair is empty
     if (ev) cudaEventRecord(ev[0], s);
-    k_contact<T><<<grid_of(D.ns, 256), 256, 0, s>>>(D);
+    launch_k(k_contact<T>, grid_of(D.ns, 256), 256, s, D);
     if (ev) cudaEventRecord(ev[1], s);
     launch_elem(D, M, s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ev) cudaEventRecord(ev[3], s);
-    k_gather<T><<<grid_of(D.nn, gather_block), gather_block, 0, s>>>(D);
+    launch_k(k_gather<T>, grid_of(D.nn, gather_block), gather_block, s, D);
     if (ev) cudaEventRecord(ev[4], s);
-    k_tail<T><<<1, 256, 0, s>>>(D);
+    launch_k(k_tail<T>, 1, 256, s, D);
     if (ev) cudaEventRecord(ev[5], s);
     return cudaGetLastError();
   }
   const bool concurrent = side != nullptr && ev == nullptr && D.nc > 0;
   if (ev) cudaEventRecord(ev[0], s);
-  k_contact<T><<<grid_of(D.ns, 256), 256, 0, s>>>(D);
+  launch_k(k_contact<T>, grid_of(D.ns, 256), 256, s, D);
   if (ev) cudaEventRecord(ev[1], s);
   if (concurrent) {
     cudaEventRecord(fork, s);
@@ -264,12 +306,12 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
   }
   launch_hex(D, M, s);
   if (ev) cudaEventRecord(ev[2], s);
-  if (!concurrent && D.nc > 0) k_coh<T><<<grid_of(D.nc, 128), 128, 0, s>>>(D, M);
+  if (!concurrent && D.nc > 0) launch_k(k_coh<T>, grid_of(D.nc, 128), 128, s, D, M);
   if (concurrent) cudaStreamWaitEvent(s, join, 0);
   if (ev) cudaEventRecord(ev[3], s);
-  k_gather<T><<<grid_of(D.nn, gather_block), gather_block, 0, s>>>(D);
+  launch_k(k_gather<T>, grid_of(D.nn, gather_block), gather_block, s, D);
   if (ev) cudaEventRecord(ev[4], s);
-  k_tail<T><<<1, 256, 0, s>>>(D);
+  launch_k(k_tail<T>, 1, 256, s, D);
   if (ev) cudaEventRecord(ev[5], s);
   return cudaGetLastError();
 }
