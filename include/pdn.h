@@ -163,7 +163,8 @@ typedef struct {
                               0..3 hex kernel (interface kernel on a forked stream)
                               with an occupancy target of 4, 5, 6 or 3 blocks/SM;
                               4..7 one mixed hex + interface kernel with the same
-                              targets.  The environment variable PDN_HEX_VARIANT
+                              targets (never chosen by the autotuner, which times
+                              0..3).  The environment variable PDN_HEX_VARIANT
                               (0..7) fixes it instead (no timing, tune_ms 0) */
   int32_t reserved;
   double tune_ms[12];      /* mean time of an internal-force pass with each variant when
