@@ -151,6 +151,39 @@ def test_batch_ragged_steps_and_info(pkg):
     b.close()
 
 
+@pytest.mark.parametrize("schedule", ["0", "1"])
+def test_batch_plates_without_surface_or_interfaces(pkg, schedule, monkeypatch):
+    """A plate without contact surface (no contact tiles: its element tiles
+    depend directly on its previous tail) and a plate without interface
+    elements, next to a regular plate, in both schedules: each follows the
+    same plate stepped alone."""
+    monkeypatch.setenv("PDN_BATCH_SCHEDULE", schedule)
+    base = _cases(3, 8, 2000, 6000, fp64=False)
+    w_nosurf = dataclasses.replace(base[0], plate=dataclasses.replace(base[0].plate,
+                                                                      surf=np.zeros(0, dtype=np.int32)))
+    p1 = base[1].plate
+    lay = list(p1.ply_angle_deg)
+    Lx, Ly, H = p1.dims
+    nx, ny, _ = p1.grid
+    w_nocoh = dataclasses.replace(base[1], plate=pi.make_plate(Lx, Ly, H, nx, ny, lay, 1, cohesive=False))
+    ws = [w_nosurf, w_nocoh, base[2]]
+    assert ws[0].plate.n_surf == 0 and ws[1].plate.n_coh == 0 and ws[2].plate.n_coh > 0
+    b = _batch(pkg, ws, False)
+    pkg.pdn_batch_step(b, 400)
+    for c, w in zip(b.plates, ws):
+        s = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+        s.step(400)
+        assert pkg.pdn_get_info(c)["step"] == 400
+        d1, d2 = pkg.pdn_get_state(c)[0], s.state()[0]
+        assert _rel(d1, d2) < 1e-5
+        f1, f2 = pkg.pdn_contact_force(c)[2], s.force_history()
+        assert np.abs(f1 - f2).max() <= 1e-5 * max(np.abs(f2).max(), 1e-300)
+        s.close()
+    assert np.abs(pkg.pdn_contact_force(b.plates[0])[2]).max() == 0.0  # no surface, no contact
+    assert np.abs(pkg.pdn_contact_force(b.plates[1])[2]).max() > 0.0
+    b.close()
+
+
 def test_batch_requires_every_striker(pkg):
     ws = _cases(2, 3, 1000, 2000, fp64=False)
     b = pkg.pdn_batch_init([w.plate for w in ws], [w.material for w in ws])

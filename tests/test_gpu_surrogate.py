@@ -165,3 +165,29 @@ def test_impact_with_learned_law(pkg, trained):
     assert np.abs(dl - de).max() <= 5e-2 * np.abs(de).max()
     ge.close()
     gl.close()
+
+
+def test_empty_training_box_falls_back_to_the_exact_law(pkg, trained):
+    """With a training box that contains no point every Gauss point takes the
+    exact law: the run follows the exact-law run to FP32 rounding (the two
+    hex kernels evaluate the same formulas in a different order)."""
+    s, _, _ = trained
+    p, sc = pkg.pdn_sur_get_params(s)
+    s2 = pkg.pdn_sur_create(_mat(), LC)
+    sc2 = sc.copy()
+    sc2[40:50] = 1e30   # lo
+    sc2[50:60] = -1e30  # hi
+    pkg.pdn_sur_set_params(s2, p, sc2)
+    w = pi.damage_fp32_plate(nx=32, ny=48, Lx=25.0, Ly=37.5, H=4.4, mass=5.5e-3 / 16, steps=1500)
+    ge = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+    gl = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+    pkg.pdn_set_surrogate(gl.ctx, s2, 0.9)
+    ge.step(1500)
+    gl.step(1500)
+    de, dl = ge.state()[0], gl.state()[0]
+    assert np.abs(dl - de).max() <= 1e-4 * np.abs(de).max()
+    fe, fl = ge.force_history(), gl.force_history()
+    assert fe.max() > 0.0 and abs(fl.max() - fe.max()) <= 1e-4 * fe.max()
+    s2.close()
+    ge.close()
+    gl.close()
