@@ -178,7 +178,10 @@ typedef struct {
  * node-to-element CSR map used for the deterministic force gather, and
  * allocate all device state (displacement, velocity, history double buffers).
  * Initial state: d = v = 0, damage thresholds r = 1, plastic strain 0,
- * interface thresholds 0 (Algorithms 4, 5).  On failure *out is NULL. */
+ * interface thresholds 0 (Algorithms 4, 5), and the acceleration a^0 of the
+ * momentum equation at step 0 (Sec. 2.2.1; no contact at t^0): the gravity
+ * acceleration on every free degree of freedom.  One internal-force pass runs
+ * on the device for it.  On failure *out is NULL. */
 int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat,
                   const pdn_options *opt);
 

@@ -621,6 +621,8 @@ static void gather_u(const orc_model *M, const double *d, const int32_t *conn, d
 }
 
 /* Create: X is SoA [3][nn] as delivered by the input generator. */
+static void acceleration_of_state(orc_model *M);
+
 orc_model *orc_create(int64_t nn, int64_t nh, int64_t nc, int64_t ns, const double *X_soa,
                       const int32_t *hex, const int32_t *coh, const int8_t *ply_hex,
                       const double *ply_angle, int32_t n_plies, const uint8_t *fixed,
@@ -769,6 +771,10 @@ orc_model *orc_create(int64_t nn, int64_t nh, int64_t nc, int64_t ns, const doub
   M->fhist_cap = fhist_cap;
   M->fhist = (double *)xcalloc((size_t)(fhist_cap > 0 ? fhist_cap : 1), sizeof(double));
   M->axis[2] = -1.0;
+  /* The discrete momentum equation (Sec. 2.2.1) holds at step 0 as well:
+   * a^0 = m^-1 (f^e - f^i(d^0)); with d^0 = 0 and no contact at t^0 this is
+   * the gravity acceleration on every free degree of freedom. */
+  acceleration_of_state(M);
   return M;
 }
 
@@ -843,6 +849,18 @@ void orc_internal_force(orc_model *M, double *f_out_soa) {
 }
 
 /* One time step n -> n+1 (Algorithm 1 with the reset loop of Algorithm 2). */
+/* Acceleration of the installed state (d, v) without contact, from the
+ * momentum equation of Sec. 2.2.1: a = m^-1 (m g - f^i(d)) on free degrees
+ * of freedom, 0 on fixed ones.  The history is left as it is. */
+static void acceleration_of_state(orc_model *M) {
+  internal_forces(M, M->d, M->hist, M->hist_new, M->rD, M->rD_new);
+  const double *g = M->opt.gravity;
+  for (int64_t j = 0; j < M->nn; ++j)
+    for (int i = 0; i < 3; ++i)
+      M->a[j * 3 + i] =
+          ((M->fixed[j] >> i) & 1) ? 0.0 : (M->mass[j] * g[i] - M->fi[j * 3 + i]) / M->mass[j];
+}
+
 static int one_step(orc_model *M) {
   int64_t nn = M->nn, ns = M->ns;
   double dt = M->dt, phi = M->opt.phi;
@@ -1049,12 +1067,7 @@ void orc_set_state(orc_model *M, const double *d, const double *v) {
       M->d[j * 3 + i] = ((M->fixed[j] >> i) & 1) ? 0.0 : d[i * M->nn + j];
       M->v[j * 3 + i] = ((M->fixed[j] >> i) & 1) ? 0.0 : v[i * M->nn + j];
     }
-  internal_forces(M, M->d, M->hist, M->hist_new, M->rD, M->rD_new);
-  const double *g = M->opt.gravity;
-  for (int64_t j = 0; j < M->nn; ++j)
-    for (int i = 0; i < 3; ++i)
-      M->a[j * 3 + i] =
-          ((M->fixed[j] >> i) & 1) ? 0.0 : (M->mass[j] * g[i] - M->fi[j * 3 + i]) / M->mass[j];
+  acceleration_of_state(M);
 }
 
 void orc_get_impactor(const orc_model *M, double out[10]) {

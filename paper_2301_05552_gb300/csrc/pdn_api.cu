@@ -136,6 +136,21 @@ int set_mode(pdn_ctx *ctx, int32_t mode, int64_t target) {
   return PDN_OK;
 }
 
+// Acceleration of the installed state, without contact (momentum equation of
+// Sec. 2.2.1): one pass in MODE_PRIME computes a = m^-1 (m g - f^i(d)) and
+// the predictor of Eq. (TW) from it, then makes the installed state the
+// committed one; history, step and time stay as they are.
+static int prime_state(pdn_ctx *ctx) {
+  int rc = set_mode(ctx, MODE_PRIME, ctx->ctl_host->step);
+  if (rc) return rc;
+  cudaError_t e = run_pass(ctx, nullptr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "prime pass");
+  rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "non-finite state installed");
+  return PDN_OK;
+}
+
 // Material constants in precision T from the double-precision record.
 template <typename T>
 int fill_mat(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_plies, int damage_on,
@@ -680,6 +695,12 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     wire(ctx->Dd, double{});
   else
     wire(ctx->Df, float{});
+  // a^0 from the momentum equation at step 0 (Sec. 2.2.1): d^0 = 0 and no
+  // contact at t^0, so the gravity acceleration on every free degree of
+  // freedom; the first step then predicts d^1 and v^1 from it
+  rc = read_ctl(ctx);
+  if (!rc) rc = prime_state(ctx);
+  if (rc) return die(rc, std::string("initial acceleration: ") + ctx->err);
   *out = ctx;
   return PDN_OK;
 }
@@ -918,14 +939,7 @@ int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v) {
   else
     k_mirror<float4><<<grid_of(nn, 256), 256, 0, ctx->stream>>>(dd[b], ctx->Df.u4[b], nn);
   PDN_CU(cudaGetLastError(), "mirror kernel");
-  rc = set_mode(ctx, MODE_PRIME, ctx->ctl_host->step);
-  if (rc) return rc;
-  cudaError_t e = run_pass(ctx, nullptr);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "prime pass");
-  rc = read_ctl(ctx);
-  if (rc) return rc;
-  if (ctx->ctl_host->status) return fail(ctx, ctx->ctl_host->status, "non-finite state installed");
-  return PDN_OK;
+  return prime_state(ctx);
 }
 
 int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {

@@ -77,7 +77,8 @@ def seeded_quasi_isotropic_layup(n_plies: int, seed: int) -> List[float]:
 
 def make_plate(Lx: float, Ly: float, H: float, nx: int, ny: int,
                ply_angles: Sequence[float], elems_per_ply: int = 1,
-               cohesive: bool = True, clamp: str = "edges") -> Plate:
+               cohesive: bool = True, clamp: str = "edges",
+               window: tuple = (125.0, 75.0), clamp_radius: float = 5.0) -> Plate:
     """Structured plate on [0,Lx]x[0,Ly]x[0,H].
 
     Elements are numbered x fastest, then y, then through the thickness
@@ -85,6 +86,12 @@ def make_plate(Lx: float, Ly: float, H: float, nx: int, ny: int,
     top.  A new node layer is created at every ply interface whose two plies
     differ in angle (when ``cohesive``), and an interface element joins the two
     coincident layers there.
+
+    clamp = "frame" reads the drop-weight supports of Sec. 3.2 (ASTM D7136):
+    the plate rests on a frame with a centred window of ``window`` (mm); the
+    bottom nodes on the window's edge take its contact (z held), and the top
+    nodes within ``clamp_radius`` of the window's four corners take the
+    rubber-tipped clamps (all three components held).
     """
     ply_angles = [float(a) for a in ply_angles]
     n_plies = len(ply_angles)
@@ -155,6 +162,22 @@ def make_plate(Lx: float, Ly: float, H: float, nx: int, ny: int,
         fixed[X[2] == 0.0] = 7
     elif clamp == "none":
         fixed = np.zeros(X.shape[1], dtype=np.uint8)
+    elif clamp == "frame":
+        fixed = np.zeros(X.shape[1], dtype=np.uint8)
+        wx, wy = window
+        x0, x1 = 0.5 * (Lx - wx), 0.5 * (Lx + wx)
+        y0, y1 = 0.5 * (Ly - wy), 0.5 * (Ly + wy)
+        hx, hy = Lx / nx, Ly / ny
+        tol_x, tol_y = 0.5 * hx, 0.5 * hy
+        x, y, z = X
+        # nodes of the window's edge line (within half an element)
+        near_x = ((np.abs(x - x0) <= tol_x) | (np.abs(x - x1) <= tol_x)) & (y >= y0 - tol_y) & (y <= y1 + tol_y)
+        near_y = ((np.abs(y - y0) <= tol_y) | (np.abs(y - y1) <= tol_y)) & (x >= x0 - tol_x) & (x <= x1 + tol_x)
+        fixed[(z == 0.0) & (near_x | near_y)] = 4
+        top = z == layer_z[-1]
+        for cx in (x0, x1):
+            for cy in (y0, y1):
+                fixed[top & ((x - cx) ** 2 + (y - cy) ** 2 <= clamp_radius ** 2)] = 7
     else:
         raise ValueError(clamp)
     surf = np.arange((n_layers - 1) * per_layer, n_layers * per_layer, dtype=np.int32)
@@ -187,6 +210,26 @@ def material_im7_like_config(t_ply: float, strengths=(2300.0, 60.0, 90.0),
         G12=5000.0, G13=5000.0, G23=E2 / (2.0 * (1.0 + nu23)),
         XT=XT, XC=1531.0, YT=YT, YC=199.8, SL=SL, alpha0_deg=alpha0,
         GXT=81.5, GXC=106.3, GYT=GIc, GYC=GSL / np.cos(np.radians(alpha0)), GSL=GSL,
+        Sp=62.0, Kp=0.1936,
+        GIc=GIc, GIIc=GIIc, tauI=YT, tauII=SL, eta=1.45, KI=50.0 * E2 / t_ply,
+        spread=spread, seed=seed,
+    )
+
+
+def material_as4_8552(t_ply: float, spread: float = 0.05, seed: int = 0) -> Dict[str, float]:
+    """The AS4/8552 column of the paper's material table (Table 1): elastic
+    constants, strengths (Y_T and S_L as listed), fracture toughnesses,
+    plasticity, interface toughnesses (tau_I = Y_T, tau_II = S_L) and the BK
+    exponent.  The interface penalty stiffness follows the 50 E_T / t rule of
+    Sec. 2.3.2 with t the element-layer thickness (the table's K_coh units are
+    unreadable)."""
+    E2 = 7630.0
+    YT, SL, GIc, GIIc = 74.2, 94.36, 0.28, 0.79
+    return dict(
+        rho=1.59e-9, E1=128.0e3, E2=E2, E3=E2, nu12=0.35, nu13=0.35, nu23=0.45,
+        G12=4358.0, G13=4358.0, G23=2631.0,
+        XT=2300.0, XC=1531.0, YT=YT, YC=199.8, SL=SL, alpha0_deg=53.0,
+        GXT=81.5, GXC=106.3, GYT=GIc, GYC=1.313, GSL=GIIc,
         Sp=62.0, Kp=0.1936,
         GIc=GIc, GIIc=GIIc, tauI=YT, tauII=SL, eta=1.45, KI=50.0 * E2 / t_ply,
         spread=spread, seed=seed,
@@ -263,6 +306,27 @@ def large_fp32_plate(steps: int = 5000) -> Workload:
     5.5 kg striker at 4 m/s."""
     return damage_fp32_plate(nx=400, ny=600, plies=16, elems_per_ply=2, speed=4000.0,
                              steps=steps)
+
+
+def as4_frame_plate(nx: int = 207, ny: int = 138, Lx: float = 150.0, Ly: float = 100.0,
+                    window=(125.0, 75.0), clamp_radius: float = 5.0, mass: float = 5.0e-3,
+                    speed: float = 2780.0, steps: int = 20000, fp64: bool = False,
+                    seed: int = 0) -> Workload:
+    """The AS4/8552 drop-weight coupon of Sec. 3.2: 150x100 mm,
+    [45_4/0_4/-45_4/90_4]_S with 0.181 mm plies (5.79 mm), one element per
+    four-ply cluster (the 90_8 cluster in two) and 0.725 mm in plane as the
+    paper's base mesh, interfaces between clusters of different angle, frame
+    and clamp supports (make_plate clamp="frame"), striker R = 8 mm, 5 kg at
+    2.78 m/s (19.3 J), gap 0.01 mm, gravity 9.81 m/s^2 on plate and striker,
+    Tchamwa-Wielgosz phi = 1.033."""
+    t_cluster = 4 * 0.181
+    lay = [45.0, 0.0, -45.0, 90.0, 90.0, -45.0, 0.0, 45.0]
+    plate = make_plate(Lx, Ly, 8 * t_cluster, nx, ny, lay, 1, cohesive=True, clamp="frame",
+                       window=window, clamp_radius=clamp_radius)
+    mat = material_as4_8552(t_ply=t_cluster, seed=seed)
+    name = f"as4_plate{Lx:g}x{Ly:g}x{8 * t_cluster:.2f}_{nx}x{ny}x8_{'fp64' if fp64 else 'fp32'}_frame"
+    return Workload(name, plate, mat, fp64, True, True, 8.0, mass, speed, 0.01, 0.5, steps,
+                    phi=1.033, gravity=(0.0, 0.0, -9810.0))
 
 
 def batch_plates(n: int = 64, seed: int = 0, hex_min: int = 8000, hex_max: int = 400000,

@@ -430,6 +430,29 @@ def test_tw_phi1_is_central_difference():
     assert np.abs(vM - vh).max() < 1e-10 * np.abs(vh).max()
 
 
+def test_tw_phi_free_fall_closed_form():
+    """An unconstrained plate falling under gravity (rigid translation: no
+    strain, no internal force) with the Tchamwa-Wielgosz parameter
+    phi = 1.033 of Sec. 2.2.1: v^{n+1} = v^n + dt g and d^{n+1} = d^n + dt v^n
+    + phi dt^2 g give v^n = n dt g and d^n = dt^2 g (n(n-1)/2 + n phi)
+    exactly; phi = 1 would give the central-difference value n^2/2 + n/2."""
+    plate = pi.make_plate(4.0, 4.0, 1.0, 2, 2, [0.0, 90.0], 1, cohesive=False, clamp="none")
+    mat = pi.material_im7_like_config(t_ply=0.5, spread=0.0)
+    g = -9810.0
+    M = oracle.Model(plate, mat, phi=1.033, gravity=(0.0, 0.0, g))
+    M.set_impactor(1.0, 1e-3, (2.0, 2.0, 1e6), (0.0, 0.0, -1.0))  # far away: no contact
+    n = 60
+    assert M.step(n) == 0
+    dt = M.info()["dt"]
+    d, v, _ = M.state()
+    assert np.allclose(v[2], n * dt * g, rtol=1e-12, atol=0.0)
+    assert np.allclose(d[2], dt * dt * g * (n * (n - 1) / 2.0 + n * 1.033), rtol=1e-11, atol=0.0)
+    # (m g)/m rounds differently at nodes of different lumped mass: strains,
+    # and with them in-plane motion, at round-off level only
+    assert np.abs(d[:2]).max() < 1e-8 * abs(d[2]).max()
+    assert np.abs(v[:2]).max() < 1e-8 * abs(v[2]).max()
+
+
 def test_central_difference_stability_limit():
     """One free node on a hex: the scheme is stable for dt < 2/omega_max and
     unstable above (omega from the node's 3x3 stiffness by finite differences)."""
