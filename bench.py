@@ -33,6 +33,12 @@ against the same plates advanced one after another by the plain pdn_step
 hex8 (7.68M elements, two per ply, 4 m/s): 5,000 steps by default, without the
 end-to-end leg.
 
+--workload as4 runs the AS4/8552 coupon of Sec. 3.2: 150x100 mm, 207x138x8
+hex8 (228,528 elements, 0.725 mm, one per ply cluster), interfaces between
+clusters, frame and clamp supports, Table 1 material, 5 kg striker R = 8 mm at
+2.78 m/s, gravity, Tchamwa-Wielgosz phi = 1.033; by default the paper's whole
+5 ms of simulated time (214,000 steps).
+
 --workload surrogate trains the learned intralaminar law (generation and
 training times reported), measures its held-out accuracy, and runs the
 100x150 mm plate with the learned law against the exact law (step time and
@@ -176,6 +182,8 @@ def workload_for(args):
     import pdn_inputs as pi
     if getattr(args, "workload", "plate") == "large":
         return pi.large_fp32_plate(steps=args.steps)
+    if getattr(args, "workload", "plate") == "as4":
+        return pi.as4_frame_plate(steps=args.steps, seed=args.seed)
     return pi.damage_fp32_plate(seed=args.seed)
 
 
@@ -592,7 +600,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: 20000 for the plate, 500 for batch64)")
+                    help="timed steps (default: 20000 for the plate, 5000 large, 214000 as4, 500 batch64)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--seed", type=int, default=0)
@@ -600,10 +608,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["plate", "large", "batch64", "surrogate"], default="plate")
+    ap.add_argument("--workload", choices=["plate", "large", "as4", "batch64", "surrogate"], default="plate")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"batch64": 500, "large": 5000}.get(args.workload, 20000)
+        args.steps = {"batch64": 500, "large": 5000, "as4": 214000}.get(args.workload, 20000)
     if args.warmup < 3 and args.impl == "gpu":
         args.warmup = 3
     ws, rank, local = dist_setup()

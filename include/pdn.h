@@ -46,8 +46,8 @@ extern "C" {
 #define PDN_E_RELEASE_LIMIT (-5) /* a step still had adhesive contact nodes after
                                     max_release_iters repetitions (Algorithm 2) */
 #define PDN_E_TIMEOUT (-6)       /* reserved: a bounded device wait gave up */
-#define PDN_E_UNSTABLE (-7)      /* material/mesh gives no stable step or a snap-back
-                                    softening law (2 E G <= lc X^2) */
+#define PDN_E_UNSTABLE (-7)      /* material/mesh gives no stable step (and, for the
+                                    learned law, a snap-back length: pdn_surrogate.h) */
 #define PDN_E_STATE (-8)         /* call out of order (e.g. step before set_impactor) */
 
 /* Precision of the element force, damage and cohesive updates.  Nodal

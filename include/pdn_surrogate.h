@@ -41,7 +41,9 @@ typedef struct pdn_surrogate pdn_surrogate;
 /* Create a surrogate for a material (nominal strengths, spread ignored) and
  * crack-band length lc (mm) on the current device; parameters initialised
  * from seed (He-uniform weights, zero biases), identity scaling.  stream as
- * in pdn_options. */
+ * in pdn_options.  PDN_E_UNSTABLE when lc is at or past the snap-back length
+ * 2 E G / X^2 of any mode: there the exact law drops to zero stress at onset,
+ * a jump in the thresholds that the network does not represent. */
 int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint64_t seed, void *stream);
 
 /* Training set: n_paths seeded elastic-strain paths of steps_per_path

@@ -176,7 +176,9 @@ void orc_stiffness(const orc_material *m, double C[6][6]) {
  *     rFT = max(rFT, phiFT, rFC); rMC = max(rMC, phiMC);
  *     rMT = max(rMT, phiMT, rMC).
  *  5. Damage: d(r) = 1 - exp(A (1 - r)) / r with
- *     A = 2 lc X^2 / (2 E G - lc X^2)  (crack band: G/lc per unit volume).
+ *     A = 2 lc X^2 / (2 E G - lc X^2)  (crack band: G/lc per unit volume);
+ *     A = +inf (d = 1 once r > 1) for elements at or past the snap-back
+ *     length lc >= 2 E G / X^2, the limit of the law from below.
  *     D1 = dFT or dFC by the sign of sigma~11 (E1, XT|XC, GXT|GXC);
  *     D2 = dMT or dMC by the sign of sigma~22 (E2, YT|YC, GYT|GYC);
  *     D6 = d6(rMT) with (G12, SL, GSL).
@@ -192,8 +194,13 @@ static double damage_of(double r, double A) {
   return 1.0 - exp(A * (1.0 - r)) / r;
 }
 
+/* Past the snap-back length (lc X^2 >= 2 E G) no exponential branch with
+ * onset at X dissipates G/lc; the law takes its limit from below, A -> +inf:
+ * the stress drops to zero right after onset (dissipation X^2/(2E) per
+ * volume, the least possible with that onset). */
 static double softening_A(double lc, double X, double E, double G) {
-  return 2.0 * lc * X * X / (2.0 * E * G - lc * X * X);
+  const double lx2 = lc * X * X, den = 2.0 * E * G - lx2;
+  return den > 0.0 ? 2.0 * lx2 / den : INFINITY;
 }
 
 static void cdm_point_c(const orc_material *m, const double C0[6][6], const double H[6][6],

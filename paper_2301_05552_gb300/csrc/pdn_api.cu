@@ -379,16 +379,6 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     vol[e] = V;
     const double lc = std::cbrt(V);
     dtb = std::min(dtb, lc * sqrho);
-    if (opt->damage_on) {
-      // crack-band limit of the softening laws (2 E G > lc X^2), with the
-      // largest seeded strengths
-      const double f = 1.0 + m.spread;
-      const double chk[5][3] = {{m.E1, m.GXT, m.XT * f}, {m.E1, m.GXC, m.XC}, {m.E2, m.GYT, m.YT * f},
-                                {m.E2, m.GYC, m.YC}, {m.G12, m.GSL, m.SL * f}};
-      for (auto &c : chk)
-        if (!(2.0 * c[0] * c[1] > lc * c[2] * c[2]))
-          return die(PDN_E_UNSTABLE, "element too large for the crack-band softening law (2 E G <= lc X^2)");
-    }
   }
   // Axis-aligned boxes whose corner coordinates coincide exactly in pairs in
   // the element precision: then the higher trilinear modes of X vanish

@@ -178,10 +178,12 @@ __device__ __forceinline__ double strength_factor(const Mat<double> &M, int64_t 
 // element length and the damaged compliance are those of the oracle (see the
 // header of oracle/pdn_oracle.c); the element length is computed lazily (only
 // once some threshold exceeds 1).
+// At or past the snap-back length (lc X^2 >= 2 E G) the law takes its limit
+// from below, A = +inf: the stress drops to zero right after onset.
 template <typename T>
 __device__ __forceinline__ T soft_A(T lc, T X, T E, T G) {
-  T lx2 = lc * X * X;
-  return T(2) * lx2 / (T(2) * E * G - lx2);
+  const T lx2 = lc * X * X, den = T(2) * E * G - lx2;
+  return den > T(0) ? T(2) * lx2 / den : static_cast<T>(INFINITY);
 }
 template <typename T>
 __device__ __forceinline__ T dmg(T r, T A) {

@@ -808,7 +808,8 @@ int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint
   s->law.L.iSL2 = 1.0 / (M.SL * M.SL);
   s->law.L.etaL = M.SL * M.etaLc;
   s->law.lc = lc;
-  // the crack band must not snap back at this length (as pdn_init_mesh checks)
+  // below the snap-back length only: past it the law drops to zero stress at
+  // onset (d jumps at r = 1), which a smooth network cannot represent
   const double X[5] = {M.XT, M.XC, M.YT, M.YC, M.SL}, E[5] = {M.E1, M.E1, M.E2, M.E2, M.G12},
                G[5] = {M.GXT, M.GXC, M.GYT, M.GYC, M.GSL};
   for (int k = 0; k < 5; ++k)

@@ -329,6 +329,17 @@ def as4_frame_plate(nx: int = 207, ny: int = 138, Lx: float = 150.0, Ly: float =
                     phi=1.033, gravity=(0.0, 0.0, -9810.0))
 
 
+def reduced_as4_frame_plate(nx: int = 40, ny: int = 28, mass: float = 2.0e-4, steps: int = 2000,
+                            fp64: bool = True, seed: int = 0) -> Workload:
+    """A cut-down AS4/8552 coupon for parity runs: the element size, layup,
+    material, clamps and striker of as4_frame_plate on nx x ny elements
+    (0.725 mm spacing), with the frame window and clamp radius scaled with the
+    plate and, by default, the striker mass scaled with its area."""
+    Lx, Ly = nx * 150.0 / 207.0, ny * 100.0 / 138.0
+    return as4_frame_plate(nx=nx, ny=ny, Lx=Lx, Ly=Ly, window=(Lx * 125.0 / 150.0, Ly * 75.0 / 100.0),
+                           clamp_radius=5.0 * Lx / 150.0, mass=mass, steps=steps, fp64=fp64, seed=seed)
+
+
 def batch_plates(n: int = 64, seed: int = 0, hex_min: int = 8000, hex_max: int = 400000,
                  steps: int = 2000, fp64: bool = False) -> List[Workload]:
     """Independent impact cases for a batched launch: plate sizes log-uniform

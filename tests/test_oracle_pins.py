@@ -183,6 +183,39 @@ def test_crack_band_dissipation_equals_fracture_energy(mode):
     assert np.abs(sig).max() == pytest.approx(X, rel=1e-3)
 
 
+@pytest.mark.parametrize("mode", ["FT", "FC", "MT", "MC", "S12"])
+def test_past_snap_back_length_the_stress_drops_at_onset(mode):
+    """An element at or past the crack band's snap-back length
+    lc = 2 E G / X^2 cannot soften exponentially with onset at X; the law
+    takes its limit from below (A -> +inf).  Pinned against that limit: past
+    the length the peak is still X, the stress is zero right after onset and
+    the work is the elastic triangle X^2/(2E); just below the length the
+    regular law dissipates G/lc, which tends to the same X^2/(2E) (MT with
+    g = G_YT/G_SL = 1, a loading function linear in stress)."""
+    mat = zero_poisson_material(**(dict(GSL=0.3, GYT=0.3) if mode == "MT" else {}))
+    comp, sign, G = {"FT": (0, 1, mat["GXT"]), "FC": (0, -1, mat["GXC"]),
+                     "MT": (1, 1, mat["GYT"]), "MC": (1, -1, mat["GYC"]),
+                     "S12": (3, 1, mat["GSL"])}[mode]
+    X = {"FT": mat["XT"], "FC": mat["XC"], "MT": mat["YT"], "MC": mat["YC"], "S12": mat["SL"]}[mode]
+    E = {0: mat["E1"], 1: mat["E2"], 3: mat["G12"]}[comp]
+    l_snap = 2.0 * E * G / (X * X)
+    tri = X * X / (2.0 * E)
+    for f in (1.0, 1.5):
+        es, sig = _uniaxial_path(mat, comp, sign, f * l_snap, n=20001, r_end_factor=2.0)
+        assert np.abs(sig).max() == pytest.approx(X, rel=1e-3)
+        e0 = X / E
+        after = np.abs(es) > e0 * (1.0 + 1e-9)
+        assert after.any() and (sig[after] == 0.0).all()
+        assert np.trapezoid(sig, es) == pytest.approx(tri, rel=2e-3)
+    # just below the length: the regular law, G/lc, close to the triangle
+    lc = 0.995 * l_snap
+    A = 2 * lc * X * X / (2 * E * G - lc * X * X)
+    es, sig = _uniaxial_path(mat, comp, sign, lc, r_end_factor=1.0 + 28.0 / A)
+    W = np.trapezoid(sig, es)
+    assert W == pytest.approx(G / lc, rel=2e-3)
+    assert W == pytest.approx(tri, rel=1e-2)
+
+
 @pytest.mark.parametrize("comp,sign,key", [(0, 1, "XT"), (0, -1, "XC"), (1, 1, "YT"),
                                            (1, -1, "YC"), (3, 1, "SL")])
 def test_damage_onset_at_strength(comp, sign, key):
