@@ -244,9 +244,12 @@ def test_invalid_arguments(pkg):
     dup.surf = np.concatenate([dup.surf, dup.surf[:1]])
     with pytest.raises(pkg.PdnError):
         pkg.pdn_init_mesh(dup, mat, damage_on=False)
-    # 1 mm elements are too coarse for the compressive matrix softening law
+    # 1 mm elements, past the compressive matrix law's snap-back length, are
+    # accepted (the law drops to zero stress at onset there); the learned law
+    # is refused at that length
+    pkg.pdn_init_mesh(plate, mat, damage_on=True).close()
     with pytest.raises(pkg.PdnError) as ei:
-        pkg.pdn_init_mesh(plate, mat, damage_on=True)
+        pkg.pdn_sur_create(mat, 1.0)
     assert ei.value.code == -7
     ctx = pkg.pdn_init_mesh(plate, mat, damage_on=False)
     with pytest.raises(pkg.PdnError) as ei:
