@@ -199,7 +199,12 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
  * trial damage history; deterministic CSR gather; lumped-mass accelerations
  * with the contact reactions; release of adhesive nodes (f^c . n < 0,
  * Eq. anodes) with repetition of the step (Algorithm 2); Tchamwa-Wielgosz
- * update (Sec. 2.2.1).  Returns after the work has completed on the stream.
+ * update (Sec. 2.2.1).  A repetition evaluates again only the elements of the
+ * released nodes and the nodes of those elements (everything else has the
+ * same inputs as before and keeps its values); the environment variable
+ * PDN_FULL_REPEAT=1, read by pdn_init_mesh, makes repetitions evaluate every
+ * element and node, with the same results.  Returns after the work has
+ * completed on the stream.
  * Errors: PDN_E_STATE without a striker, PDN_E_NONFINITE,
  * PDN_E_RELEASE_LIMIT (both sticky), PDN_E_CUDA. */
 int pdn_step(pdn_ctx *ctx, int64_t nsteps);

@@ -464,7 +464,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
-    uint8_t *nflag, *act[2], *rel, *pflag[2], *cflag[2];
+    uint8_t *nflag, *act[2], *rel, *rmark_e, *rmark_n, *pflag[2], *cflag[2];
     double *Xs, *mass, *d[2], *v[2], *nrm, *lam, *trial, *fhist, *fout;
     Ctl *ctl;
     Striker *imp;
@@ -500,6 +500,8 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     }
     P.fe = A.take<char>(ts * 4 * (nh + nc) * 8);
     P.rel = A.take<uint8_t>(ns1);
+    P.rmark_e = A.take<uint8_t>(nh + nc);
+    P.rmark_n = A.take<uint8_t>(nn);
     P.nrm = A.take<double>(sizeof(double) * 3 * ns1);
     P.lam = A.take<double>(sizeof(double) * ns1);
     P.trial = A.take<double>(sizeof(double) * 6 * ns1);
@@ -524,7 +526,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   int32_t *d_hex = P.hex, *d_coh = P.coh, *d_surf = P.surf, *d_surf_of = P.surf_of, *d_row = P.row, *d_col = P.col;
   int8_t *d_ply = P.ply;
   char *d_X4 = P.X4, *d_imass = P.imass, *d_fe = P.fe;
-  uint8_t *d_nflag = P.nflag, *d_rel = P.rel;
+  uint8_t *d_nflag = P.nflag, *d_rel = P.rel, *d_rmark_e = P.rmark_e, *d_rmark_n = P.rmark_n;
   double *d_Xs = P.Xs, *d_mass = P.mass, *d_nrm = P.nrm, *d_lam = P.lam, *d_trial = P.trial, *d_fhist = P.fhist,
          *d_fout = P.fout;
   double *d_d[2] = {P.d[0], P.d[1]}, *d_v[2] = {P.v[0], P.v[1]};
@@ -612,6 +614,8 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   }
   chk(cudaMemset(d_fe, 0, ts * 4 * (nh + nc) * 8));
   chk(cudaMemset(d_rel, 0, std::max<int64_t>(ns, 1)));
+  chk(cudaMemset(d_rmark_e, 0, nh + nc));
+  chk(cudaMemset(d_rmark_n, 0, nn));
   chk(cudaMemset(d_nrm, 0, sizeof(double) * 3 * std::max<int64_t>(ns, 1)));
   chk(cudaMemset(d_lam, 0, sizeof(double) * std::max<int64_t>(ns, 1)));
   Ctl c0{};
@@ -664,6 +668,12 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     }
     D.fe = reinterpret_cast<V4 *>(d_fe);
     D.rel = d_rel;
+    // PDN_FULL_REPEAT=1: repeated passes evaluate every element and node
+    // again (the reference for the local repetition, same results)
+    const char *fr = std::getenv("PDN_FULL_REPEAT");
+    const bool full = fr != nullptr && fr[0] == '1' && fr[1] == '\0';
+    D.rmark_e = full ? nullptr : d_rmark_e;
+    D.rmark_n = full ? nullptr : d_rmark_n;
     D.nrm = d_nrm;
     D.lam = d_lam;
     D.trial = d_trial;

@@ -171,6 +171,28 @@ __device__ __forceinline__ double strength_factor(const Mat<double> &M, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Local repetition of a step (Algorithm 2).  A repeated pass differs from the
+// pass before it only at the released nodes, which the contact item puts back
+// to their state before projection.  Only the elements around those nodes
+// (marked by the contact item) and the nodes of those elements (marked by the
+// element items) are evaluated again; every other element force and nodal
+// update of the previous pass came from identical inputs and stands.  An item
+// consumes its mark (clears it), so no mark outlives its pass; a mark left
+// behind would only cost one more evaluation with the same result.  Without
+// mark buffers (null) a repeated pass evaluates everything again.
+__device__ __forceinline__ bool repeat_take(uint8_t *mark, int64_t i) {
+  if (mark == nullptr) return true;
+  if (mark[i] == 0) return false;
+  mark[i] = 0;
+  return true;
+}
+__device__ __forceinline__ void repeat_mark_nodes(uint8_t *mark, const int nd[8]) {
+  if (mark == nullptr) return;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) mark[nd[a]] = 1;
+}
+
+// ---------------------------------------------------------------------------
 // Intralaminar law (Algorithm 4) at one Gauss point, ply axes.
 // eps: engineering strain [11 22 33 12 13 23]; h: history in/out
 // {rFT, rFC, rMT, rMC, gp12, gp13, pbar}; sig: nominal stress.

@@ -126,6 +126,11 @@ struct Dev {
   // contact
   uint8_t *act[2];         // [ns] contact set by step parity
   uint8_t *rel;            // [ns] released in the current step
+  // local repetition of a step: marks of the elements ([nh + nc], hexes then
+  // interfaces) and nodes ([nn]) that a repeated pass evaluates again; zero
+  // outside a repeated pass (null: repeated passes evaluate everything)
+  uint8_t *rmark_e;
+  uint8_t *rmark_n;
   double *nrm;             // [3][ns]
   double *lam;             // [ns]
   double *trial;           // [6][ns] pre-projection d and v of active nodes

@@ -110,6 +110,9 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
       u.w = T(0);
       D.u4[cur][j] = u;
       D.act[spar][s] = 0;
+      // the elements of the released node are evaluated again
+      if (D.rmark_e != nullptr)
+        for (int k = D.row[j], k1 = D.row[j + 1]; k < k1; ++k) D.rmark_e[D.col[k] >> 3] = 1;
     }
   }
 }
@@ -143,11 +146,13 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
   using V4 = float4;
   const Ctl *ctl = D.ctl;
   if (e >= D.nh) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, e)) return;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const V4 *__restrict__ U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   float ua[8][3];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -350,6 +355,7 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
   if (e >= D.nh) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, e)) return;
   const int64_t nh = D.nh;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
@@ -357,6 +363,7 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   const T *__restrict__ hin = D.hist[hb] + e;
   T *__restrict__ hout = D.hist[hb ^ 1] + e;
   // An element whose points all still hold the initial history skips the
@@ -553,6 +560,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
   if (c >= D.nc) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, D.nh + c)) return;
   const int64_t nc = D.nc;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
@@ -560,6 +568,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   constexpr int QX[4] = {-1, 1, 1, -1}, QY[4] = {-1, -1, 1, 1};
   // the upper face coincides with the lower one in the reference
   // configuration (zero thickness), so the lower face gives the mid-surface
@@ -902,6 +911,7 @@ template <typename T>
 __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
   using V4 = typename Vec4T<T>::type;
   if (j >= D.nn) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_n, j)) return;
   Ctl *ctl = D.ctl;
   const int64_t nn = D.nn;
   const bool stepping = mode != MODE_FORCES;

@@ -467,8 +467,12 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nh = D.nh;
   if (e - lane >= nh) return;  // the whole warp is past the last element
-  const bool act = e < nh;
-  const int64_t el = act ? e : nh - 1;
+  // a repeated pass evaluates only the marked elements (local repetition);
+  // the others follow the warp on their own element and store nothing
+  bool act = e < nh;
+  if (mode == MODE_REPEAT && act) act = repeat_take(D.rmark_e, e);
+  if (!__any_sync(0xffffffffu, act)) return;
+  const int64_t el = e < nh ? e : nh - 1;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
   const float4 *__restrict__ U = D.u4[ub];
@@ -614,6 +618,7 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
     }
   }
   if (!act) return;
+  if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][el] = (pristine_in && !dirty) ? 1 : 0;
   float f[8][3];
   from_modes(C, f);

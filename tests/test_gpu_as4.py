@@ -165,3 +165,35 @@ def test_batch_of_coupons_with_gravity_matches_oracle(pkg):
         assert _rel(dg, do) < F64_TOL
         assert o.force_history().max() > 0.0
     b.close()
+
+
+@pytest.mark.parametrize("fp64,variant", [(True, None), (False, None), (False, "4")])
+def test_local_repeat_equals_full_repeat(pkg, monkeypatch, fp64, variant):
+    """Repetitions of a step after releases (Algorithm 2) evaluate only the
+    elements of the released nodes and their nodes; with PDN_FULL_REPEAT=1
+    they evaluate everything.  The cut-down coupon through 2000 steps with
+    repetitions gives bitwise the same state, contact set, force history and
+    damage fields either way (FP64, FP32, and the FP32 kernel that evaluates
+    hexes and interfaces in one launch)."""
+    if variant is not None:
+        monkeypatch.setenv("PDN_HEX_VARIANT", variant)
+    w = pi.reduced_as4_frame_plate(fp64=fp64)
+    runs = []
+    for full in ("0", "1"):
+        monkeypatch.setenv("PDN_FULL_REPEAT", full)
+        g = pkg.Solver(w)
+        g.step(2000)
+        d, v, imp = g.state()
+        act, lam = pkg.pdn_get_contact(g.ctx)
+        fields = [pkg.pdn_damage_field(g.ctx, f) for f in ("D1", "D2", "D6", "DCOH")]
+        runs.append((d, v, act, lam, g.force_history(), fields, g.info()))
+        g.close()
+    (d0, v0, a0, l0, f0, k0, i0), (d1, v1, a1, l1, f1, k1, i1) = runs
+    assert i0["n_repeats"] == i1["n_repeats"] > 5
+    if variant is not None:
+        assert i0["hex_variant"] == i1["hex_variant"] == int(variant)
+    assert np.array_equal(d0, d1) and np.array_equal(v0, v1)
+    assert np.array_equal(a0, a1) and np.array_equal(l0, l1)
+    assert np.array_equal(f0, f1)
+    for x, y in zip(k0, k1):
+        assert np.array_equal(x, y)

@@ -191,3 +191,24 @@ def test_empty_training_box_falls_back_to_the_exact_law(pkg, trained):
     s2.close()
     ge.close()
     gl.close()
+
+
+def test_learned_law_local_repeat_equals_full_repeat(pkg, trained, monkeypatch):
+    """The hex kernel of the learned law evaluates, in a repeated pass, only
+    the elements of released nodes (its warps still run together); a run
+    with PDN_FULL_REPEAT=1 (every element again) is bitwise the same."""
+    s, _, _ = trained
+    w = pi.damage_fp32_plate(nx=32, ny=48, Lx=25.0, Ly=37.5, H=4.4, mass=5.5e-3 / 16, steps=3000)
+    runs = []
+    for full in ("0", "1"):
+        monkeypatch.setenv("PDN_FULL_REPEAT", full)
+        g = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+        pkg.pdn_set_surrogate(g.ctx, s, 0.9)
+        g.step(2500)
+        d, v, _ = g.state()
+        runs.append((d, v, g.force_history(), pkg.pdn_damage_field(g.ctx, "D2"), g.info()["n_repeats"]))
+        g.close()
+    (d0, v0, f0, k0, r0), (d1, v1, f1, k1, r1) = runs
+    assert r0 == r1
+    assert np.array_equal(d0, d1) and np.array_equal(v0, v1)
+    assert np.array_equal(f0, f1) and np.array_equal(k0, k1)
