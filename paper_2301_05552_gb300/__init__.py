@@ -31,6 +31,8 @@ __all__ = [
     "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
     "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate",
     "pdn_sur_destroy", "pdn_sur_last_error", "pdn_sur_get_data", "SUR_PARAMS", "SUR_SCALING",
+    "pdn_mesh_multiply", "pdn_refined_get_info", "pdn_refined_get", "pdn_init_refined", "pdn_refined_destroy",
+    "pdn_refined_last_error", "Refined",
     "PDN_FP64", "PDN_FP32_FORCE", "FIELDS", "KERNELS",
 ]
 
@@ -47,7 +49,9 @@ EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force",
            "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
            "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
            "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate",
-           "pdn_sur_destroy", "pdn_sur_last_error", "pdn_sur_get_data"]
+           "pdn_sur_destroy", "pdn_sur_last_error", "pdn_sur_get_data",
+           "pdn_mesh_multiply", "pdn_refined_get_info", "pdn_refined_get", "pdn_init_refined",
+           "pdn_refined_destroy", "pdn_refined_last_error"]
 SUR_PARAMS = 9674
 SUR_SCALING = 60
 
@@ -63,6 +67,12 @@ class MeshDesc(C.Structure):
                 ("X", C.POINTER(C.c_double)), ("hex", C.POINTER(C.c_int32)), ("coh", C.POINTER(C.c_int32)),
                 ("ply_of_hex", C.POINTER(C.c_int8)), ("ply_angle_deg", C.POINTER(C.c_double)),
                 ("n_plies", C.c_int32), ("fixed", C.POINTER(C.c_uint8)), ("surf", C.POINTER(C.c_int32))]
+
+
+class RefinedInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
+                ("n_edges", C.c_int64), ("n_faces", C.c_int64), ("levels", C.c_int32), ("pad", C.c_int32),
+                ("device_ms", C.c_double)]
 
 
 MATERIAL_KEYS = ("rho", "E1", "E2", "E3", "nu12", "nu13", "nu23", "G12", "G13", "G23",
@@ -171,6 +181,17 @@ def lib():
             L.pdn_sur_last_error.restype = C.c_char_p
             for name in ("pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
                          "pdn_sur_gradient", "pdn_sur_get_params", "pdn_sur_set_params", "pdn_set_surrogate"):
+                getattr(L, name).restype = C.c_int
+            L.pdn_mesh_multiply.argtypes = [C.POINTER(vp), C.POINTER(MeshDesc), C.c_int32, vp]
+            L.pdn_refined_get_info.argtypes = [vp, C.POINTER(RefinedInfo)]
+            L.pdn_refined_get.argtypes = [vp, dp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int8),
+                                          C.POINTER(C.c_uint8), C.POINTER(C.c_int32)]
+            L.pdn_init_refined.argtypes = [C.POINTER(vp), vp, C.POINTER(Material), C.POINTER(Options)]
+            L.pdn_refined_destroy.argtypes = [vp]
+            L.pdn_refined_destroy.restype = None
+            L.pdn_refined_last_error.argtypes = [vp]
+            L.pdn_refined_last_error.restype = C.c_char_p
+            for name in ("pdn_mesh_multiply", "pdn_refined_get_info", "pdn_refined_get", "pdn_init_refined"):
                 getattr(L, name).restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
                          "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
@@ -634,3 +655,93 @@ class Solver:
 
     def close(self):
         self.ctx.close()
+
+
+# ---------------------------------------------------------------------------
+# Mesh multiplication on the device (include/pdn_mmu.h)
+
+class Refined:
+    """A pdn_refined handle: a divided mesh held in device memory."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().pdn_refined_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pdn_refined_last_error(r: Optional[Refined]) -> str:
+    return (lib().pdn_refined_last_error(r.handle if r is not None else None) or b"").decode()
+
+
+def _rcheck(r, rc):
+    if rc < 0:
+        raise PdnError(int(rc), pdn_refined_last_error(r))
+    return rc
+
+
+def pdn_mesh_multiply(plate, ndivi: int, stream: Optional[int] = None) -> Refined:
+    """pdn_mesh_multiply: divide ``plate`` (pdn_inputs.Plate fields) ndivi
+    times on the current device."""
+    L = lib()
+    m, keep = _mesh_desc(plate)
+    if stream is None:
+        stream = _current_stream()
+    h = C.c_void_p()
+    rc = L.pdn_mesh_multiply(C.byref(h), C.byref(m), int(ndivi), stream)
+    if rc < 0:
+        raise PdnError(rc, (L.pdn_refined_last_error(None) or b"").decode())
+    return Refined(h)
+
+
+def pdn_refined_get_info(r: Refined) -> dict:
+    info = RefinedInfo()
+    _rcheck(r, lib().pdn_refined_get_info(r.handle, C.byref(info)))
+    return {k: getattr(info, k) for k, _ in RefinedInfo._fields_ if k != "pad"}
+
+
+def pdn_refined_get(r: Refined) -> dict:
+    """The divided mesh on the host: X [3, n], hex [n_hex, 8], coh [n_coh, 8],
+    ply_of_hex, fixed, surf."""
+    i = pdn_refined_get_info(r)
+    X = np.empty((3, i["n_nodes"]), np.float64)
+    hx = np.empty((i["n_hex"], 8), np.int32)
+    ch = np.empty((i["n_coh"], 8), np.int32)
+    ply = np.empty(i["n_hex"], np.int8)
+    fx = np.empty(i["n_nodes"], np.uint8)
+    sf = np.empty(i["n_surf"], np.int32)
+    _rcheck(r, lib().pdn_refined_get(r.handle, _ptr(X, C.c_double), _ptr(hx, C.c_int32),
+                                     _ptr(ch, C.c_int32) if ch.size else None, _ptr(ply, C.c_int8),
+                                     _ptr(fx, C.c_uint8), _ptr(sf, C.c_int32) if sf.size else None))
+    return dict(X=X, hex=hx, coh=ch, ply_of_hex=ply, fixed=fx, surf=sf)
+
+
+def pdn_init_refined(r: Refined, material: dict, precision: int = PDN_FP32_FORCE, damage_on: bool = True,
+                     plasticity_on: bool = True, max_release_iters: int = 8, phi: float = 1.0, dt: float = 0.0,
+                     dt_safety: float = 0.5, gravity=(0.0, 0.0, 0.0), history_cap: int = 1 << 20,
+                     stream: Optional[int] = None) -> Context:
+    """pdn_init_refined: a solver context on the divided mesh."""
+    L = lib()
+    if stream is None:
+        stream = _current_stream()
+    o = _options(precision, damage_on, plasticity_on, max_release_iters, phi, dt, dt_safety, gravity,
+                 history_cap, stream)
+    mat = _material(material)
+    h = C.c_void_p()
+    rc = L.pdn_init_refined(C.byref(h), r.handle, C.byref(mat), C.byref(o))
+    if rc < 0:
+        raise PdnError(rc, (L.pdn_last_error(None) or b"").decode() or pdn_refined_last_error(r))
+    i = pdn_refined_get_info(r)
+    return Context(h, i["n_nodes"], i["n_hex"], i["n_coh"], i["n_surf"], stream)
+
+
+def pdn_refined_destroy(r: Refined):
+    r.close()
