@@ -286,7 +286,7 @@ __global__ void k_hex_children(const int32_t *hex, const int8_t *ply, int64_t nh
   load_hex(hex, e, n);
   int32_t L[27];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) L[kCorner[a][0] / 2 + 3 * (kCorner[a][1] / 2) + 9 * (kCorner[a][2] / 2)] = n[a];
+  for (int a = 0; a < 8; ++a) L[kCorner[a][0] + 3 * kCorner[a][1] + 9 * kCorner[a][2]] = n[a];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int p = kEdge[k][0], q = kEdge[k][1];
