@@ -39,6 +39,13 @@ clusters, frame and clamp supports, Table 1 material, 5 kg striker R = 8 mm at
 2.78 m/s, gravity, Tchamwa-Wielgosz phi = 1.033; by default the paper's whole
 5 ms of simulated time (214,000 steps).
 
+--workload mmu divides the AS4/8552 coupon once on the device (Algorithm 3:
+228,528 hexes and 171,396 interfaces become the paper's 0.3625 mm mesh of
+1,828,224 hexes and 685,584 interfaces) and runs the impact on the divided
+mesh: the division's device time and rate go in "mesh_multiply", the line's
+value is the step rate on the divided mesh, and the end-to-end leg starts
+from the coarse mesh on the host.
+
 --workload surrogate trains the learned intralaminar law (generation and
 training times reported), measures its held-out accuracy, and runs the
 100x150 mm plate with the learned law against the exact law (step time and
@@ -484,6 +491,140 @@ def run_batch(args, ws, rank, local):
     return 0
 
 
+def mmu_alg_bytes(nn, nh, nc, ns, nn1, ns1) -> int:
+    """Algorithmic bytes of one division level: the coarse mesh read once and
+    the divided mesh written once; per node 24 B of coordinates and 1 B of
+    constraint bits, per hex 32 B of connectivity and 1 B of ply, per
+    interface 32 B, per surface node 4 B."""
+    return (nn * 25 + nh * 33 + nc * 32 + ns * 4) + (nn1 * 25 + 8 * nh * 33 + 4 * nc * 32 + ns1 * 4)
+
+
+def run_mmu(args, ws, rank, local):
+    """Device mesh multiplication of the AS4/8552 coupon and the impact on
+    the divided mesh."""
+    import numpy as np
+    import torch
+
+    import oracle.mesh_multiply as omm
+    import paper_2301_05552_gb300 as pkg
+    import pdn_inputs as pi
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pkg.lib()
+    w = pi.as4_frame_plate(steps=args.steps, seed=args.seed)
+    coarse = w.plate
+    stream = torch.cuda.Stream()
+    opts = dict(precision=pkg.PDN_FP32_FORCE, damage_on=w.damage_on, plasticity_on=w.plasticity_on, phi=w.phi,
+                dt_safety=w.dt_safety, gravity=w.gravity, stream=stream.cuda_stream)
+    # division: one untimed call, then the device time of three calls
+    with torch.cuda.stream(stream):
+        pkg.pdn_mesh_multiply(coarse, 1, stream=stream.cuda_stream).close()
+        div_ms = []
+        for k in range(3):
+            r = pkg.pdn_mesh_multiply(coarse, 1, stream=stream.cuda_stream)
+            div_ms.append(pkg.pdn_refined_get_info(r)["device_ms"])
+            if k < 2:
+                r.close()
+        ri = pkg.pdn_refined_get_info(r)
+        ctx = pkg.pdn_init_refined(r, w.material, **opts)
+        r.close()
+    nh1, nc1, nn1, ns1 = ri["n_hex"], ri["n_coh"], ri["n_nodes"], ri["n_surf"]
+    pkg.pdn_set_impactor(ctx, *w.impactor())
+    K, W = args.steps, args.warmup
+    pkg.pdn_step(ctx, W)
+    rep0 = pkg.pdn_get_info(ctx)["n_repeats"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        ev0.record(stream)
+        pkg.pdn_step(ctx, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = max_over_ranks(dist, [ev0.elapsed_time(ev1)], "cuda")[0]
+    info = pkg.pdn_get_info(ctx)
+    repeats = info["n_repeats"] - rep0
+    value = whole_job_rate(ws, nh1 * K, ms)
+    prof = pkg.pdn_profile_kernels(ctx, args.profile_steps)
+    hex_ms = prof["hex"][0]
+    peak_gbs, peak_kind = measured_peaks()
+    alg = hex_alg_bytes(nh1, nn1)
+    achieved = alg / (hex_ms * 1e-3) / 1e9
+    fh = pkg.pdn_contact_force(ctx)[2]
+    ctx.close()
+
+    # end to end: the coarse mesh from the host, division, solver set-up, K
+    # steps, read-back of the force history and the final state
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        r2 = pkg.pdn_mesh_multiply(coarse, 1, stream=stream.cuda_stream)
+        c2 = pkg.pdn_init_refined(r2, w.material, **opts)
+        r2.close()
+        pkg.pdn_set_impactor(c2, *w.impactor())
+        pkg.pdn_step(c2, K)
+        _, _, hist = pkg.pdn_contact_force(c2)
+        d_fin, v_fin, _ = pkg.pdn_get_state(c2)
+    t_e2e = max_over_ranks(dist, [time.perf_counter() - t0], "cuda")[0]
+    c2.close()
+    h2d = (coarse.X.nbytes + coarse.hex.nbytes + coarse.coh.nbytes + coarse.ply_of_hex.nbytes
+           + coarse.fixed.nbytes + coarse.surf.nbytes + coarse.ply_angle_deg.nbytes)
+    d2h = hist.nbytes + d_fin.nbytes + v_fin.nbytes + 104
+    div = float(statistics.median(div_ms))
+    div_alg = mmu_alg_bytes(coarse.n_nodes, coarse.n_hex, coarse.n_coh, coarse.n_surf, nn1, ns1)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": W,
+        "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {
+            "workload": w.name.replace("207x138x8", "414x276x16") + "_divided_on_device",
+            "n_hex": nh1, "n_coh": nc1, "n_nodes": nn1, "n_surf": ns1, "dt_s": info["dt"],
+            "simulated_us": info["time"] * 1e6, "f_peak_N": float(fh.max()) if len(fh) else 0.0,
+            "step_repeats": int(repeats), "l2": "inputs larger than L2 (working set %.0f MB)"
+            % (info["device_bytes"] / 1e6), "parallelism": f"replicas x{ws}",
+        },
+        "mesh_multiply": {
+            "levels": 1, "coarse": {"n_hex": coarse.n_hex, "n_coh": coarse.n_coh, "n_nodes": coarse.n_nodes},
+            "divided_edges": ri["n_edges"], "divided_faces": ri["n_faces"], "device_ms": div,
+            "device_ms_each": div_ms, "divided_elements_per_s": (nh1 + nc1) / (div * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": div_alg / (div * 1e-3) / 1e9, "peak": peak_gbs,
+                         "unit": "GB/s", "frac": div_alg / (div * 1e-3) / 1e9 / peak_gbs,
+                         "alg_bytes": div_alg, "peak_kind": peak_kind},
+        },
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                     "frac": achieved / peak_gbs, "traffic": None, "kernel": "k_hex<float>",
+                     "alg_bytes_per_launch": alg, "launch_ms": hex_ms, "peak_kind": peak_kind},
+        "kernel_ms": {k: v[0] for k, v in prof.items()},
+        "e2e": {"value": whole_job_rate(ws, nh1 * K, t_e2e * 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K, "seconds": t_e2e},
+        "gpu_launches": (K + repeats) * 5 + 1,
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        # the oracle's division on a bounded sample: the cut-down coupon
+        cut = pi.reduced_as4_frame_plate(nx=80, ny=56).plate
+        t0 = time.perf_counter()
+        omm.divide_once(cut.X, cut.hex, cut.coh, cut.ply_of_hex, cut.fixed, cut.surf)
+        t_div = time.perf_counter() - t0
+        line["mesh_multiply"]["cpu_baseline"] = {
+            "value": (8 * cut.n_hex + 4 * cut.n_coh) / t_div, "unit": "divided elements/s", "cores": 1,
+            "kind": "oracle", "sample": f"one level of the 80x56 cut-down coupon ({cut.n_hex} hexes, {t_div:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_surrogate(args, ws, rank, local):
     """The learned law on the 128x192x16 plate against the exact law."""
     import numpy as np
@@ -608,7 +749,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["plate", "large", "as4", "batch64", "surrogate"], default="plate")
+    ap.add_argument("--workload", choices=["plate", "large", "as4", "mmu", "batch64", "surrogate"], default="plate")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = {"batch64": 500, "large": 5000, "as4": 214000}.get(args.workload, 20000)
@@ -621,6 +762,8 @@ def main():
         return run_batch(args, ws, rank, local)
     if args.workload == "surrogate":
         return run_surrogate(args, ws, rank, local)
+    if args.workload == "mmu":
+        return run_mmu(args, ws, rank, local)
     return run_gpu(args, ws, rank, local)
 
 
