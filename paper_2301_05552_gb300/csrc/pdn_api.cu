@@ -398,6 +398,19 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     for (int64_t e = 0; e < nh && all_boxes; ++e)
       all_boxes = opt->precision == PDN_FP64 ? is_box(e, double{}) : is_box(e, float{});
   }
+  bool all_flat_coh = true;
+  {
+    auto is_flat = [&](int64_t c, auto tag) {
+      using T = decltype(tag);
+      const int32_t *q = mesh->coh + c * 8;
+      auto P = [&](int a, int i) { return (T)mesh->X[i * nn + q[a]]; };
+      return P(0, 0) == P(3, 0) && P(1, 0) == P(2, 0) && P(0, 1) == P(1, 1) && P(2, 1) == P(3, 1) &&
+             P(0, 2) == P(1, 2) && P(0, 2) == P(2, 2) && P(0, 2) == P(3, 2) && P(1, 0) > P(0, 0) &&
+             P(3, 1) > P(0, 1);
+    };
+    for (int64_t c = 0; c < nc && all_flat_coh; ++c)
+      all_flat_coh = opt->precision == PDN_FP64 ? is_flat(c, double{}) : is_flat(c, float{});
+  }
   // node -> element-force slot CSR (hexes ascending, then interfaces ascending)
   std::vector<int32_t> row(nn + 1, 0), col((size_t)(nh + nc) * 8);
   for (int64_t k = 0; k < nh * 8; ++k) row[mesh->hex[k] + 1]++;
@@ -690,6 +703,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       D.grav_t[i] = (T)ctx->grav[i];
     }
     D.all_boxes = all_boxes ? 1 : 0;
+    D.all_flat_coh = all_flat_coh ? 1 : 0;
   };
   if (fp64)
     wire(ctx->Dd, double{});

@@ -159,7 +159,11 @@ __global__ void __launch_bounds__(kBatchBlock, MINB) k_batch(BatchArgs<T> A) {
             break;
           case TK_COH:
             if (mode < MODE_DONE)
-              for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) coh_item(sD, sM, i, mode);
+              for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x)
+                if (sD.all_flat_coh)
+                  coh_item<T, true>(sD, sM, i, mode);
+                else
+                  coh_item<T, false>(sD, sM, i, mode);
             break;
           case TK_GATHER:
             if (mode < MODE_DONE)
@@ -290,7 +294,11 @@ __global__ void __launch_bounds__(kBatchBlock, MINB) k_batch_flow(FlowArgs<T> A)
         break;
       case TK_COH:
         if (mode < MODE_DONE)
-          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) coh_item(sD, sM, i, mode);
+          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x)
+            if (sD.all_flat_coh)
+              coh_item<T, true>(sD, sM, i, mode);
+            else
+              coh_item<T, false>(sD, sM, i, mode);
         break;
       case TK_GATHER:
         if (mode < MODE_DONE)

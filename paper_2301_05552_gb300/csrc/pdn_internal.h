@@ -148,6 +148,11 @@ struct Dev {
   // every hex is an axis-aligned box whose corner coordinates coincide
   // exactly in pairs (in T): the trilinear map is affine and J is constant
   int32_t all_boxes;
+  // every interface element's lower face is an axis-aligned rectangle in a
+  // plane z = const, corners counter-clockwise from +z, coordinates equal in
+  // pairs exactly (in T): the local frame is the global axes and every
+  // point's area weight is a quarter of the rectangle
+  int32_t all_flat_coh;
   // launch configuration picked by the autotuner: hex occupancy variant
   // (0: 4 blocks of 128 per SM, 1: 5, 2: 6, 3: 3).  The variants execute the
   // same arithmetic, so the choice does not change any result.

@@ -555,7 +555,10 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
 // ---------------------------------------------------------------------------
 // Kernel 3: zero-thickness interface elements with Newton-Cotes integration
 // (Sec. 2.3.2) and the cohesive law (Algorithm 5).  One thread per element.
-template <typename T>
+// FLAT: every interface is a flat axis-aligned rectangle (Dev::all_flat_coh):
+// the frame is the global axes and all four area weights are Lx Ly / 4, so
+// only two corners of the geometry are read and no root is taken.
+template <typename T, bool FLAT>
 __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64_t c, int mode) {
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
@@ -573,12 +576,20 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   // the upper face coincides with the lower one in the reference
   // configuration (zero thickness), so the lower face gives the mid-surface
   T xm[4][3], uu[8][3];
+  if constexpr (FLAT) {
+    const V4 x0 = D.X4[nd[0]], x2 = D.X4[nd[2]];
+    xm[0][0] = x0.x;
+    xm[0][1] = x0.y;
+    xm[2][0] = x2.x;
+    xm[2][1] = x2.y;
+  } else {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const V4 xb = D.X4[nd[a]];
-    xm[a][0] = xb.x;
-    xm[a][1] = xb.y;
-    xm[a][2] = xb.z;
+    for (int a = 0; a < 4; ++a) {
+      const V4 xb = D.X4[nd[a]];
+      xm[a][0] = xb.x;
+      xm[a][1] = xb.y;
+      xm[a][2] = xb.z;
+    }
   }
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
@@ -589,7 +600,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   }
   // frame at the element centre
   T e1[3], e2[3], e3[3];
-  {
+  if constexpr (!FLAT) {
     T tx[3] = {T(0), T(0), T(0)}, ty[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -619,6 +630,22 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
 #pragma unroll
   for (int p = 0; p < 4; ++p) rv[p] = pristine_in ? T(0) : rin[(int64_t)p * nc + c];
   T f[8][3];
+  if constexpr (FLAT) {
+    const T w = T(0.25) * (xm[2][0] - xm[0][0]) * (xm[2][1] - xm[0][1]);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const T dl[3] = {uu[p + 4][0] - uu[p][0], uu[p + 4][1] - uu[p][1], uu[p + 4][2] - uu[p][2]};
+      T tau[3], r1;
+      czm(M, dl, rv[p], r1, tau);
+      rv[p] = r1;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T tg = w * tau[i];
+        f[p + 4][i] = tg;
+        f[p][i] = -tg;
+      }
+    }
+  } else {
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     const T xi = T(QX[p]), et = T(QY[p]);
@@ -648,6 +675,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
       f[p + 4][i] = tg;
       f[p][i] = -tg;
     }
+  }
   }
   const bool still = pristine_in && rv[0] == T(0) && rv[1] == T(0) && rv[2] == T(0) && rv[3] == T(0);
   if (!still) {

@@ -55,12 +55,12 @@ __global__ void __launch_bounds__(128, MINB) k_hex(Dev<T> D, Mat<T> M) {
   hex_item<T, BOX>(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_coh(Dev<T> D, Mat<T> M) {
+template <typename T, bool FLAT, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_coh(Dev<T> D, Mat<T> M) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  coh_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
+  coh_item<T, FLAT>(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 // Hex and interface elements in one launch: blocks alternate between a tile
@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(128, MINB) k_elem(Dev<T> D, Mat<T> M, int nbh,
   const int64_t i = (int64_t)idx * blockDim.x + threadIdx.x;
   if (kind == 0)
     hex_item<T, BOX>(D, M, i, mode);
+  else if (D.all_flat_coh)
+    coh_item<T, true>(D, M, i, mode);
   else
-    coh_item(D, M, i, mode);
+    coh_item<T, false>(D, M, i, mode);
 }
 
 template <typename T>
@@ -271,6 +273,28 @@ void launch_hex(const Dev<T> &D, const Mat<T> &M, cudaStream_t s) {
   }
 }
 
+// Interface kernel: the flat-rectangle specialisation when every interface
+// allows it; pdl = launched with programmatic dependent launch (not on the
+// forked side stream).
+template <typename T>
+void launch_coh(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, bool pdl) {
+  // FP32 flat interfaces fit 64 registers without spilling (8 blocks per
+  // SM); the others keep the compiler's budget
+  constexpr int kFlatMinBlocks = std::is_same<T, float>::value ? 8 : 1;
+  const int g = grid_of(D.nc, 128);
+  if (D.all_flat_coh) {
+    if (pdl)
+      launch_k(k_coh<T, true, kFlatMinBlocks>, g, 128, s, D, M);
+    else
+      k_coh<T, true, kFlatMinBlocks><<<g, 128, 0, s>>>(D, M);
+  } else {
+    if (pdl)
+      launch_k(k_coh<T, false, 1>, g, 128, s, D, M);
+    else
+      k_coh<T, false, 1><<<g, 128, 0, s>>>(D, M);
+  }
+}
+
 // One pass: contact, then the hex and interface kernels (concurrently when a
 // side stream with fork/join events is given: the interface kernel runs on the
 // side stream), then the gather and the tail.  With ev
@@ -301,12 +325,12 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
   if (concurrent) {
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
-    k_coh<T><<<grid_of(D.nc, 128), 128, 0, side>>>(D, M);
+    launch_coh(D, M, side, false);
     cudaEventRecord(join, side);
   }
   launch_hex(D, M, s);
   if (ev) cudaEventRecord(ev[2], s);
-  if (!concurrent && D.nc > 0) launch_k(k_coh<T>, grid_of(D.nc, 128), 128, s, D, M);
+  if (!concurrent && D.nc > 0) launch_coh(D, M, s, true);
   if (concurrent) cudaStreamWaitEvent(s, join, 0);
   if (ev) cudaEventRecord(ev[3], s);
   launch_k(k_gather<T>, grid_of(D.nn, gather_block), gather_block, s, D);

@@ -110,6 +110,37 @@ def test_fp32_damage_from_seeded_state(pkg):
     assert _rel(dg, do) < F32_DISP_TOL
 
 
+def _distorted(w, amp=0.06, seed=2):
+    """The plate with its node columns moved in-plane by seeded amounts (the
+    coincident interface layers move together): the hexes are no longer
+    boxes and the interfaces no longer rectangles, so the general element
+    kernels run instead of the box and flat-rectangle ones."""
+    import dataclasses
+    p = w.plate
+    rng = np.random.default_rng(seed)
+    _, col = np.unique(np.round(p.X[:2].T, 9), axis=0, return_inverse=True)
+    shift = rng.uniform(-amp, amp, size=(col.max() + 1, 2))
+    X = p.X.copy()
+    X[:2] += shift[col.ravel()].T
+    q = dataclasses.replace(p, X=X)
+    return dataclasses.replace(w, plate=q)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_distorted_mesh_matches_oracle(pkg, fp64):
+    """General hex8 and interface kernels on a distorted plate from a
+    damaging seeded state, against the oracle (FP64: contact set and 1e-9;
+    FP32: 1e-4)."""
+    w = _distorted(_damage_plate(fp64=fp64))
+    st = _damaging_state(w)
+    g, o = _run_both(pkg, w, 6, 10, state=st, check_contact=fp64)
+    dg, _, _ = g.state()
+    do, _, _ = o.state()
+    assert _rel(dg, do) < (F64_TOL if fp64 else F32_DISP_TOL)
+    hist, rD = o.history()
+    assert (hist[:, :, :4] > 1.0).any() and (rD > 0).any()
+
+
 def test_internal_force_matches_oracle(pkg):
     # FP32: nodal forces are sums of element contributions that largely cancel,
     # so the FP32 error relative to the largest nodal force is ~1e-5..1e-4
