@@ -155,7 +155,8 @@ struct Dev {
   int32_t all_flat_coh;
   // launch configuration picked by the autotuner: hex occupancy variant
   // (0: 4 blocks of 128 per SM, 1: 5, 2: 6, 3: 3).  The variants execute the
-  // same arithmetic, so the choice does not change any result.
+  // same source; results can differ at FP32 rounding between variants (the
+  // assembler's multiply-add contraction depends on the register budget).
   int32_t hex_variant;
   // learned law (FP32 box elements only): the network's parameters followed
   // by its scaling (include/pdn_surrogate.h), or nullptr for the exact law;

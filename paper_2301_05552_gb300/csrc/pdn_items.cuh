@@ -241,9 +241,51 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
     ep[3] = pfma(p2(2.0f * csn), E[1][1], pfma(p2(2.0f * (c2 - s2)), E[0][1], pmul(p2(-2.0f * csn), E[0][0])));
     ep[4] = pfma(p2(2.0f * sn), E[1][2], pmul(p2(2.0f * cs), E[0][2]));
     ep[5] = pfma(p2(2.0f * cs), E[1][2], pmul(p2(-2.0f * sn), E[0][2]));
-    // the law, one point at a time
+    // the law.  Pristine points (initial history) that stay below yield and
+    // below every onset, in both lanes, keep their history and take the
+    // effective stress as nominal stress: the same tests as cdm_plastic and
+    // cdm_damage with r = 1 and no plastic strain, in packed arithmetic.
+    // Every other pair takes the full law, one point at a time.
     float2 sm[6];
-    {
+    bool elastic = false;
+    if (pristine_in) {
+      const float2 s11 = pfma(p2(M.C13), ep[2], pfma(p2(M.C12), ep[1], pmul(p2(M.C11), ep[0])));
+      const float2 s22 = pfma(p2(M.C23), ep[2], pfma(p2(M.C22), ep[1], pmul(p2(M.C12), ep[0])));
+      const float2 s33 = pfma(p2(M.C33), ep[2], pfma(p2(M.C23), ep[1], pmul(p2(M.C13), ep[0])));
+      const float2 s12 = pmul(p2(M.G12), ep[3]), s13 = pmul(p2(M.G13), ep[4]), s23 = pmul(p2(M.G23), ep[5]);
+      bool ok = true;
+      if (M.plasticity_on) {
+        const float2 t12 = pmul(p2(M.G12), ep[3]), t13 = pmul(p2(M.G12), ep[4]);
+        const float2 tn2 = pfma(t13, t13, pmul(t12, t12));
+        const float ty2 = M.Sp * M.Sp;
+        ok = tn2.x <= ty2 && tn2.y <= ty2;
+      }
+      if (ok && M.damage_on) {
+        const float2 phiFT = pmul(pmul(p2(M.E1), ep[0]), p2(L.iXT));
+        const float2 tl2 = pfma(s13, s13, pmul(s12, s12));
+        const float2 a = pmul(s22, p2(L.iYT));
+        const float2 s23q = pmul(pmul(s23, s23), p2(M.iST2));
+        // matrix tension: (1-g) a + g a^2 + tauL^2/SL^2 + s23^2/ST^2
+        const float2 qmt = padd(pfma(tl2, p2(L.iSL2), pfma(pmul(p2(M.g), a), a, pmul(p2(M.g1), a))), s23q);
+        // matrix compression: the bound (tT^2 + s23^2)/ST^2 + tauL^2/SL^2
+        const float tTx = fmaxf(-s22.x * M.kT, 0.0f), tTy = fmaxf(-s22.y * M.kT, 0.0f);
+        const float2 tT = make_float2(tTx, tTy);
+        const float2 qmc = pfma(tl2, p2(L.iSL2), pmul(pfma(tT, tT, pmul(s23, s23)), p2(M.iST2)));
+        const float qx = s22.x >= 0.0f ? qmt.x : qmc.x, qy = s22.y >= 0.0f ? qmt.y : qmc.y;
+        const float fcx = fmaxf(-s11.x, 0.0f) * M.iXC, fcy = fmaxf(-s11.y, 0.0f) * M.iXC;
+        ok = phiFT.x <= 1.0f && phiFT.y <= 1.0f && fcx <= 1.0f && fcy <= 1.0f && qx <= 1.0f && qy <= 1.0f;
+      }
+      if (ok) {
+        sm[0] = s11;
+        sm[1] = s22;
+        sm[2] = s33;
+        sm[3] = s12;
+        sm[4] = s13;
+        sm[5] = s23;
+        elastic = true;
+      }
+    }
+    if (!elastic) {
       float el[6], hl[7], sl[6];
 #pragma unroll
       for (int k = 0; k < 6; ++k) el[k] = ep[k].x;
