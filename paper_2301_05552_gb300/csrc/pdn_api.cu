@@ -423,10 +423,20 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     for (int64_t c = 0; c < nc; ++c)
       for (int a = 0; a < 8; ++a) col[fill[mesh->coh[c * 8 + a]]++] = (int32_t)((nh + c) * 8 + a);
   }
-  // inverse map: CSR position of every element slot (the element kernels
-  // write their nodal forces there)
+  // Slots of the element forces.  When no node has more than eight
+  // incident elements (every structured laminate: 8 hexes inside a layer,
+  // 4 hexes and 4 interfaces on an interface layer), node j owns slots
+  // 8 j .. 8 j + 7, filled in CSR order and zero-padded: the gather then
+  // reads a node's slots in the same load round as its state, without the
+  // CSR row first, and sums them in the same order.  Otherwise the slots are
+  // the CSR positions.
+  int32_t maxdeg = 0;
+  for (int64_t j = 0; j < nn; ++j) maxdeg = std::max(maxdeg, row[j + 1] - row[j]);
+  const bool ell = maxdeg <= 8 && 8 * nn <= INT32_MAX;
+  const int64_t n_slots = ell ? 8 * nn : 8 * (nh + nc);
   std::vector<int32_t> pos(col.size());
-  for (size_t r = 0; r < col.size(); ++r) pos[col[r]] = (int32_t)r;
+  for (int64_t j = 0; j < nn; ++j)
+    for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = ell ? (int32_t)(8 * j + (r - row[j])) : r;
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
   double dtc = INFINITY;
@@ -511,7 +521,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       P.pflag[b] = A.take<uint8_t>((nh + 15) & ~int64_t(15));
       P.cflag[b] = A.take<uint8_t>(nc1);
     }
-    P.fe = A.take<char>(ts * 4 * (nh + nc) * 8);
+    P.fe = A.take<char>(ts * 4 * n_slots);
     P.rel = A.take<uint8_t>(ns1);
     P.rmark_e = A.take<uint8_t>(nh + nc);
     P.rmark_n = A.take<uint8_t>(nn);
@@ -625,7 +635,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
       k_fill_hist_float<<<grid_of(nh * 8 * 7, 256), 256>>>(reinterpret_cast<float *>(d_hist[b]), nh * 8, 4);
     chk(cudaGetLastError());
   }
-  chk(cudaMemset(d_fe, 0, ts * 4 * (nh + nc) * 8));
+  chk(cudaMemset(d_fe, 0, ts * 4 * n_slots));  // the padding slots stay zero
   chk(cudaMemset(d_rel, 0, std::max<int64_t>(ns, 1)));
   chk(cudaMemset(d_rmark_e, 0, nh + nc));
   chk(cudaMemset(d_rmark_n, 0, nn));
@@ -704,6 +714,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     }
     D.all_boxes = all_boxes ? 1 : 0;
     D.all_flat_coh = all_flat_coh ? 1 : 0;
+    D.ell = ell ? 1 : 0;
   };
   if (fp64)
     wire(ctx->Dd, double{});

@@ -153,6 +153,9 @@ struct Dev {
   // pairs exactly (in T): the local frame is the global axes and every
   // point's area weight is a quarter of the rectangle
   int32_t all_flat_coh;
+  // element-force slots: 1 = eight per node (slot 8 j + k holds the k-th
+  // entry of node j's CSR row, the rest stay zero), 0 = CSR positions
+  int32_t ell;
   // launch configuration picked by the autotuner: hex occupancy variant
   // (0: 4 blocks of 128 per SM, 1: 5, 2: 6, 3: 3).  The variants execute the
   // same source; results can differ at FP32 rounding between variants (the

@@ -985,7 +985,8 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
   Ctl *ctl = D.ctl;
   const int64_t nn = D.nn;
   const bool stepping = mode != MODE_FORCES;
-  const int r0 = D.row[j], r1 = D.row[j + 1];
+  const bool ell = D.ell != 0;
+  const int r0 = ell ? 0 : D.row[j], r1 = ell ? 0 : D.row[j + 1];
   int cur = 0;
   uint8_t fl = 0;
   T im = T(0);
@@ -1001,6 +1002,20 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
     }
   }
   T fx = T(0), fy = T(0), fz = T(0);
+  if (ell) {
+    // the node's eight slots (CSR order, zero padding): one load round with
+    // the node state above
+    const V4 *fs = D.fe + 8 * j;
+    V4 f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = fs[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      fx += f[k].x;
+      fy += f[k].y;
+      fz += f[k].z;
+    }
+  }
   for (int rb = r0; rb < r1; rb += 8) {
     V4 f[8];
 #pragma unroll
