@@ -141,6 +141,28 @@ def test_distorted_mesh_matches_oracle(pkg, fp64):
     assert (hist[:, :, :4] > 1.0).any() and (rD > 0).any()
 
 
+def test_csr_slots_when_a_node_has_more_than_eight_elements(pkg):
+    """Four hexes appended a second time (a doubled element: the same
+    physics for the device and the oracle) give their nodes more than eight
+    incident elements, so the element forces use CSR positions instead of
+    eight slots per node; FP64 stepping from a damaging seeded state against
+    the oracle."""
+    import dataclasses
+    w = _damage_plate(fp64=True)
+    p = w.plate
+    extra = np.arange(4) + p.n_hex // 2
+    q = dataclasses.replace(p, hex=np.concatenate([p.hex, p.hex[extra]]),
+                            ply_of_hex=np.concatenate([p.ply_of_hex, p.ply_of_hex[extra]]))
+    w = dataclasses.replace(w, plate=q)
+    deg = np.bincount(np.concatenate([q.hex.ravel(), q.coh.ravel()]), minlength=q.n_nodes)
+    assert deg.max() > 8
+    st = _damaging_state(w)
+    g, o = _run_both(pkg, w, 4, 10, state=st)
+    dg, _, _ = g.state()
+    do, _, _ = o.state()
+    assert _rel(dg, do) < F64_TOL
+
+
 def test_internal_force_matches_oracle(pkg):
     # FP32: nodal forces are sums of element contributions that largely cancel,
     # so the FP32 error relative to the largest nodal force is ~1e-5..1e-4
