@@ -437,6 +437,15 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   std::vector<int32_t> pos(col.size());
   for (int64_t j = 0; j < nn; ++j)
     for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = ell ? (int32_t)(8 * j + (r - row[j])) : r;
+  std::vector<uint32_t> rank(ell ? nh + nc : 0);
+  if (ell) {
+    for (int64_t e = 0; e < nh + nc; ++e) {
+      const int32_t *cn = e < nh ? mesh->hex + e * 8 : mesh->coh + (e - nh) * 8;
+      uint32_t w = 0;
+      for (int a = 0; a < 8; ++a) w |= (uint32_t)(pos[e * 8 + a] - 8 * cn[a]) << (3 * a);
+      rank[e] = w;
+    }
+  }
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
   double dtc = INFINITY;
@@ -485,6 +494,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   const size_t ts = fp64 ? 8 : 4;
   struct Ptrs {
     int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos;
+    uint32_t *rank;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
     uint8_t *nflag, *act[2], *rel, *rmark_e, *rmark_n, *pflag[2], *cflag[2];
@@ -509,6 +519,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     P.row = A.take<int32_t>(sizeof(int32_t) * (nn + 1));
     P.col = A.take<int32_t>(sizeof(int32_t) * (nh + nc) * 8);
     P.pos = A.take<int32_t>(sizeof(int32_t) * (nh + nc) * 8);
+    P.rank = A.take<uint32_t>(sizeof(uint32_t) * std::max<int64_t>(rank.size(), 1));
     P.mass = A.take<double>(sizeof(double) * nn);
     P.imass = A.take<char>(ts * nn);
     for (int b = 0; b < 2; ++b) {
@@ -619,6 +630,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   chk(up(d_row, row.data(), sizeof(int32_t) * (nn + 1)));
   chk(up(d_col, col.data(), sizeof(int32_t) * col.size()));
   chk(up(P.pos, pos.data(), sizeof(int32_t) * pos.size()));
+  chk(up(P.rank, rank.data(), sizeof(uint32_t) * rank.size()));
   chk(up(d_mass, mass.data(), sizeof(double) * nn));
   chk(up(d_imass, imass.data(), imass.size()));
   for (int b = 0; b < 2; ++b) {
@@ -677,6 +689,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     D.row = d_row;
     D.col = d_col;
     D.pos = P.pos;
+    D.rank = ell ? P.rank : nullptr;
     D.mass = d_mass;
     D.inv_mass = reinterpret_cast<const T *>(d_imass);
     for (int b = 0; b < 2; ++b) {

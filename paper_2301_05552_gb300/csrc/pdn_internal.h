@@ -109,6 +109,10 @@ struct Dev {
   const int32_t *row;      // [nn + 1] CSR of node -> element-force slot
   const int32_t *col;      // [nnz] slot = 8*e + k (hex), 8*(nh + c) + k (interface)
   const int32_t *pos;      // [nnz] inverse of col: CSR position of slot (e, k)
+  // with eight slots per node (ell): per element (hexes, then interfaces)
+  // the rank of each corner's slot in its node's eight, 3 bits per corner,
+  // so that slot = 8 node + rank (null otherwise)
+  const uint32_t *rank;
   const double *mass;      // [nn]
   const T *inv_mass;       // [nn]
   // state (double buffered)

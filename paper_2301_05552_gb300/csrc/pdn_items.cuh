@@ -15,6 +15,27 @@ namespace pdn {
 namespace detail {
 
 // ---------------------------------------------------------------------------
+// Slots of an element's eight nodal forces.  With eight slots per node
+// (D.rank set) slot = 8 node + rank, the node ids re-read from the
+// connectivity (still in L1 from the element's start) and the ranks packed
+// 3 bits per corner; otherwise the precomputed positions.
+template <typename T>
+__device__ __forceinline__ void element_slots(const Dev<T> &D, const int32_t *conn, int64_t e, const int4 *pos2,
+                                              uint32_t rk, int (&ps)[8]) {
+  if (D.rank != nullptr) {
+    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e);
+    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e + 1);
+    const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ps[a] = 8 * nd[a] + (int)((rk >> (3 * a)) & 7u);
+  } else {
+    const int4 p0 = __ldg(pos2), p1 = __ldg(pos2 + 1);
+    ps[0] = p0.x, ps[1] = p0.y, ps[2] = p0.z, ps[3] = p0.w;
+    ps[4] = p1.x, ps[5] = p1.y, ps[6] = p1.z, ps[7] = p1.w;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Kernel 1: contact detection and projection (Sec. 2.1, Fig. 1, Algorithm 1).
 // One thread per contact-surface node.  The striker state of the step being
 // computed (its RK4 update with the committed contact force held over the
@@ -140,7 +161,7 @@ __host__ __device__ constexpr int pair_point(int p, int l) {
 // ua (by node) and the x-y-z extents of the box (corner 6 minus corner 0).
 __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
                                                    const float (&ua)[8][3], float ex, float ey, float ez,
-                                                   bool pristine_in, int ply, const int4 *pos2);
+                                                   bool pristine_in, int ply, const int4 *pos2, uint32_t rk);
 
 __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode) {
   using V4 = float4;
@@ -163,13 +184,14 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
   }
   const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
   const bool pristine_in = D.pflag[0] != nullptr && D.pflag[ctl->hpar][e] != 0;
+  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + e) : 0u;
   hex_box_pairs_core(D, M, e, mode, ua, x6.x - x0.x, x6.y - x0.y, x6.z - x0.z, pristine_in, D.ply[e],
-                     reinterpret_cast<const int4 *>(D.pos) + 2 * e);
+                     reinterpret_cast<const int4 *>(D.pos) + 2 * e, rk);
 }
 
 __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
                                                    const float (&ua)[8][3], float ex, float ey, float ez,
-                                                   bool pristine_in, int ply, const int4 *pos2) {
+                                                   bool pristine_in, int ply, const int4 *pos2, uint32_t rk) {
   const Ctl *ctl = D.ctl;
   const int64_t nh = D.nh;
   const int hb = ctl->hpar;
@@ -371,9 +393,8 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
   float f[8][3];
   from_modes(C, f);
-  const int4 p0 = pos2[0];
-  const int4 p1 = pos2[1];
-  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+  int ps[8];
+  element_slots(D, D.hex, e, pos2, rk, ps);
 #pragma unroll
   for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
 }
@@ -612,6 +633,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   const V4 *__restrict__ U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
+  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + D.nh + c) : 0u;
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   constexpr int QX[4] = {-1, 1, 1, -1}, QY[4] = {-1, -1, 1, 1};
@@ -725,9 +747,8 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
     for (int p = 0; p < 4; ++p) rout[(int64_t)p * nc + c] = rv[p];
   }
   if (D.cflag[0] != nullptr) D.cflag[hb ^ 1][c] = still ? 1 : 0;
-  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c));
-  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c) + 1);
-  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+  int ps[8];
+  element_slots(D, D.coh, c, reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c), rk, ps);
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     V4 o;
