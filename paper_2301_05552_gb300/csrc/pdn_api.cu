@@ -660,6 +660,7 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   Striker s0{};
   s0.axis[2] = -1.0;
   s0.M = 1.0;
+  s0.iM = 1.0;
   for (int i = 0; i < 3; ++i) s0.g[i] = ctx->grav[i];
   chk(up(ctx->imp_dev, &s0, sizeof(Striker)));
   chk(cudaMemset(d_imp_step, 0, sizeof(StrikerStep)));
@@ -757,6 +758,7 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
   }
   s.R = radius;
   s.M = mass;
+  s.iM = 1.0 / mass;
   s.has = 1;
   PDN_CU(cudaMemcpyAsync(ctx->imp_dev, &s, sizeof(Striker), cudaMemcpyHostToDevice, ctx->stream), "set impactor");
   StrikerStep *ss = ctx->precision == PDN_FP64 ? ctx->Dd.imp_step : ctx->Df.imp_step;

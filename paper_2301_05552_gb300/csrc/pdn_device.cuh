@@ -418,7 +418,7 @@ __device__ __forceinline__ void czm(const Mat<T> &M, const T (&dl)[3], T rin, T 
 __device__ __forceinline__ void striker_rk4(const Striker &S, double dt, double (&c1)[3],
                                             double (&w1)[3], double (&aI)[3]) {
   double ga[3];
-  const double iM = 1.0 / S.M;
+  const double iM = S.iM;
 #pragma unroll
   for (int i = 0; i < 3; ++i) ga[i] = S.g[i] - S.F[i] * iM;
   const double an = ga[0] * S.axis[0] + ga[1] * S.axis[1] + ga[2] * S.axis[2];

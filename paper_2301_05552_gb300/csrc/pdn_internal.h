@@ -45,6 +45,7 @@ struct Striker {
   double F[3];        // contact force on the plate at step n: sum_j lambda_j n_j
   double axis[3];     // unit impact direction (the only free degree of freedom)
   double R, M;
+  double iM;  // 1 / M, set with M (the per-pass update then needs no FP64 division)
   double g[3];
   int32_t has;
   int32_t pad;

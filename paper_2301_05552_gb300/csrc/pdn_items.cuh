@@ -779,7 +779,11 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
   Ctl c;
   Striker S;
   StrikerStep ss;
+  int nf = 0;
   if (threadIdx.x == 0) {
+    // the pass's non-finite flag (raised by the gather, which has completed)
+    // is read here, early, so that its latency overlaps the reduction
+    nf = *(volatile int *)&ctl->nonfinite;
     c = *ctl;
     if (stepping) {
       S = *D.imp;
@@ -936,7 +940,6 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     na += ti[0][k];
     nd += ti[1][k];
   }
-  const int nf = *(volatile int *)&ctl->nonfinite;
   c.nonfinite = 0;  // for the next pass
   if (mode == MODE_FORCES) {
     c.mode = MODE_DONE;
