@@ -15,6 +15,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pdn.h"
@@ -352,6 +353,25 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   };
 
   // --- set-up on the host: lumped mass, lengths, stable steps -------------
+  // The element loop runs on the host's cores in contiguous chunks: each
+  // element's nodal mass contributions (summed over its Gauss points) go to
+  // its own slots, and the nodes sum them afterwards in element order, so the
+  // result does not depend on the number of threads.
+  const int n_threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  auto parallel_chunks = [&](int64_t n, auto &&body) {
+    const int nt = n < 4096 ? 1 : n_threads;
+    const int64_t chunk = (n + nt - 1) / nt;
+    if (nt == 1) {
+      body(int64_t(0), n, 0);
+      return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
+      if (b < e) th.emplace_back([&, b, e, t]() { body(b, e, t); });
+    }
+    for (auto &x : th) x.join();
+  };
   std::vector<double> mass(nn, 0.0);
   std::vector<double> vol(nh);
   double cmax = 0.0;
@@ -365,20 +385,36 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   }
   double dtb = INFINITY;
   const double sqrho = std::sqrt(m.rho / cmax);
-  for (int64_t e = 0; e < nh; ++e) {
-    double Xe[8][3], detJ[8], N[8][8];
-    for (int a = 0; a < 8; ++a)
-      for (int i = 0; i < 3; ++i) Xe[a][i] = mesh->X[i * nn + mesh->hex[e * 8 + a]];
-    hex_gauss(Xe, detJ, N);
-    double V = 0.0;
-    for (int g = 0; g < 8; ++g) {
-      if (!(detJ[g] > 0)) return die(PDN_E_ARG, "hex with non-positive Jacobian (element " + std::to_string(e) + ")");
-      V += detJ[g];
-      for (int a = 0; a < 8; ++a) mass[mesh->hex[e * 8 + a]] += m.rho * N[g][a] * detJ[g];
-    }
-    vol[e] = V;
-    const double lc = std::cbrt(V);
-    dtb = std::min(dtb, lc * sqrho);
+  {
+    std::vector<double> cm((size_t)nh * 8);
+    std::vector<double> dtb_t(n_threads, INFINITY);
+    std::vector<int64_t> bad_t(n_threads, -1);
+    parallel_chunks(nh, [&](int64_t b, int64_t e1, int t) {
+      for (int64_t e = b; e < e1; ++e) {
+        double Xe[8][3], detJ[8], N[8][8];
+        for (int a = 0; a < 8; ++a)
+          for (int i = 0; i < 3; ++i) Xe[a][i] = mesh->X[i * nn + mesh->hex[e * 8 + a]];
+        hex_gauss(Xe, detJ, N);
+        double V = 0.0, s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int g = 0; g < 8; ++g) {
+          if (!(detJ[g] > 0)) {
+            bad_t[t] = e;
+            return;
+          }
+          V += detJ[g];
+          for (int a = 0; a < 8; ++a) s[a] += m.rho * N[g][a] * detJ[g];
+        }
+        for (int a = 0; a < 8; ++a) cm[e * 8 + a] = s[a];
+        vol[e] = V;
+        dtb_t[t] = std::min(dtb_t[t], std::cbrt(V) * sqrho);
+      }
+    });
+    for (int t = 0; t < n_threads; ++t)
+      if (bad_t[t] >= 0)
+        return die(PDN_E_ARG, "hex with non-positive Jacobian (element " + std::to_string(bad_t[t]) + ")");
+    for (int t = 0; t < n_threads; ++t) dtb = std::min(dtb, dtb_t[t]);
+    for (int64_t e = 0; e < nh; ++e)
+      for (int a = 0; a < 8; ++a) mass[mesh->hex[e * 8 + a]] += cm[e * 8 + a];
   }
   // Axis-aligned boxes whose corner coordinates coincide exactly in pairs in
   // the element precision: then the higher trilinear modes of X vanish
@@ -449,7 +485,9 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
   double dtc = INFINITY;
-  for (int64_t c = 0; c < nc; ++c) {
+  std::vector<double> dtc_t(n_threads, INFINITY);
+  parallel_chunks(nc, [&](int64_t c0, int64_t c1, int t) {
+  for (int64_t c = c0; c < c1; ++c) {
     double hmin = INFINITY;
     for (int side = 0; side < 2; ++side) {
       const int32_t *fn = mesh->coh + c * 8 + side * 4;
@@ -479,8 +517,10 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
         hmin = std::min(hmin, vol[e] / A);
       }
     }
-    if (std::isfinite(hmin)) dtc = std::min(dtc, std::sqrt(m.rho * hmin / m.KI));
+    if (std::isfinite(hmin)) dtc_t[t] = std::min(dtc_t[t], std::sqrt(m.rho * hmin / m.KI));
   }
+  });
+  for (int t = 0; t < n_threads; ++t) dtc = std::min(dtc, dtc_t[t]);
   ctx->dt_bulk = dtb;
   ctx->dt_coh = dtc;
   const double safety = opt->dt_safety > 0 ? opt->dt_safety : 0.5;
