@@ -2,14 +2,16 @@
 // Eq. mmu, Algorithm 3).  The division, the numbering and the coordinate
 // rule are stated in include/pdn_mmu.h.
 //
-// GPU design: no sort and no hash table.  Every edge (face) of the mesh is
-// owned by the lowest (hex, local edge) [(hex, local face)] that has it.  One
-// thread per (hex, local edge) finds the owner by searching the hexes around
-// the edge's smaller node in a node -> hex CSR built on the device (the order
-// inside a CSR row does not matter: only the minimum is kept).  Owner flags
-// and an exclusive scan give each divided edge its rank among the owners in
-// (hex, local edge) order, which is the order of first appearance of a
-// serial pass; faces likewise.  Children are then written by one thread per
+// GPU design: no global sort and no hash table.  Every edge (face) of the
+// mesh is owned by the lowest (hex, local edge) [(hex, local face)] that has
+// it.  A node -> slot CSR (slot = 8 hex + local corner) is built on the device
+// and each row sorted; one thread per (hex, local edge) merges the rows of
+// the edge's two nodes and takes the first hex in which they are joined by an
+// edge (the local edge follows from the two local corners), one thread per
+// (hex, local face) merges the rows of two opposite corners and checks the
+// other two.  Owner flags and an exclusive scan give each divided edge its
+// rank among the owners in (hex, local edge) order, which is the order of
+// first appearance of a serial pass; faces likewise.  Children are then written by one thread per
 // parent from a 3x3x3 lattice of node ids (3x3 per face for interfaces).
 #include <cuda_runtime.h>
 
@@ -80,11 +82,102 @@ __global__ void k_degree(const int32_t *hex, int64_t n8, int32_t *deg) {
   const int64_t t = gid();
   if (t < n8) atomicAdd(&deg[hex[t]], 1);
 }
+// the rows hold slots 8 hex + local corner; filled in any order, then sorted
+// per node, so that the searches below meet the hexes in ascending order
 __global__ void k_fill(const int32_t *hex, int64_t n8, int32_t *cursor, int32_t *col) {
   const int64_t t = gid();
   if (t >= n8) return;
   const int32_t pos = atomicAdd(&cursor[hex[t]], 1);
-  col[pos] = (int32_t)(t >> 3);
+  col[pos] = (int32_t)t;
+}
+__global__ void k_sort_rows(const int32_t *row, int64_t nn, int32_t *col) {
+  const int64_t j = gid();
+  if (j >= nn) return;
+  const int32_t r0 = row[j], r1 = row[j + 1];
+  for (int32_t i = r0 + 1; i < r1; ++i) {
+    const int32_t v = col[i];
+    int32_t k = i - 1;
+    while (k >= r0 && col[k] > v) {
+      col[k + 1] = col[k];
+      --k;
+    }
+    col[k + 1] = v;
+  }
+}
+
+// local edge joining two corners (-1: not an edge), and the face on which
+// two corners are diagonal (-1: not diagonal on any face)
+__constant__ int8_t kEdgeOf[8][8] = {{-1, 0, -1, 3, 8, -1, -1, -1},  {0, -1, 1, -1, -1, 9, -1, -1},
+                                     {-1, 1, -1, 2, -1, -1, 10, -1}, {3, -1, 2, -1, -1, -1, -1, 11},
+                                     {8, -1, -1, -1, -1, 4, -1, 7},  {-1, 9, -1, -1, 4, -1, 5, -1},
+                                     {-1, -1, 10, -1, -1, 5, -1, 6}, {-1, -1, -1, 11, 7, -1, 6, -1}};
+__constant__ int8_t kFaceDiag[8][8] = {{-1, -1, 0, -1, -1, 2, -1, 5}, {-1, -1, -1, 0, 2, -1, 3, -1},
+                                       {0, -1, -1, -1, -1, 3, -1, 4}, {-1, 0, -1, -1, 5, -1, 4, -1},
+                                       {-1, 2, -1, 5, -1, -1, 1, -1}, {2, -1, 3, -1, -1, -1, -1, 1},
+                                       {-1, 3, -1, 4, 1, -1, -1, -1}, {5, -1, 4, -1, -1, 1, -1, -1}};
+
+// first hex (ascending) in which nodes a and b are joined by an edge: its
+// code 12 h + local edge, or -1
+__device__ int64_t common_edge(const int32_t *row, const int32_t *col, int32_t a, int32_t b) {
+  int32_t i = row[a], i1 = row[a + 1], k = row[b], k1 = row[b + 1];
+  while (i < i1 && k < k1) {
+    const int32_t si = col[i], sk = col[k];
+    const int32_t hi = si >> 3, hk = sk >> 3;
+    if (hi < hk) {
+      ++i;
+    } else if (hk < hi) {
+      ++k;
+    } else {
+      const int ed = kEdgeOf[si & 7][sk & 7];
+      if (ed >= 0) return 12 * (int64_t)hi + ed;
+      ++i;
+      ++k;
+    }
+  }
+  return -1;
+}
+
+// first hex (ascending) with a face whose node set is {q0, q1, q2, q3} (q0
+// and q2 opposite): its code 6 h + local face, or -1.  The hexes holding q0
+// and q2 are met in order; where the two are diagonal on a face, the other
+// diagonal decides, otherwise all six faces are compared as node sets.
+__device__ int64_t common_face(const int32_t *hex, const int32_t *row, const int32_t *col, const int32_t q[4]) {
+  int32_t sq[4] = {q[0], q[1], q[2], q[3]};
+  sort4(sq);
+  int32_t i = row[q[0]], i1 = row[q[0] + 1], k = row[q[2]], k1 = row[q[2] + 1];
+  while (i < i1 && k < k1) {
+    const int32_t si = col[i], sk = col[k];
+    const int32_t hi = si >> 3, hk = sk >> 3;
+    if (hi < hk) {
+      ++i;
+      continue;
+    }
+    if (hk < hi) {
+      ++k;
+      continue;
+    }
+    const int64_t h = hi;
+    const int ff = kFaceDiag[si & 7][sk & 7];
+    if (ff >= 0) {
+      const int c0 = si & 7;
+      const bool first = c0 == kFace[ff][0] || c0 == kFace[ff][2];
+      const int32_t o1 = hex[8 * h + kFace[ff][first ? 1 : 0]], o3 = hex[8 * h + kFace[ff][first ? 3 : 2]];
+      if ((o1 == q[1] && o3 == q[3]) || (o1 == q[3] && o3 == q[1])) return 6 * h + ff;
+    } else {
+      int32_t n[8];
+      load_hex(hex, h, n);
+      for (int f2 = 0; f2 < 6; ++f2) {
+        int32_t v[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) v[a] = n[kFace[f2][a]];
+        sort4(v);
+        if (v[0] == sq[0] && v[1] == sq[1] && v[2] == sq[2] && v[3] == sq[3]) return 6 * h + f2;
+      }
+    }
+    ++i;
+    ++k;
+  }
+  return -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -97,21 +190,9 @@ __global__ void k_edge_owner(const int32_t *hex, int64_t nh, const int32_t *row,
   const int64_t e = t / 12;
   const int k = (int)(t - 12 * e);
   const int32_t a = hex[8 * e + kEdge[k][0]], b = hex[8 * e + kEdge[k][1]];
-  const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
-  int64_t best = t;
-  for (int32_t i = row[lo], i1 = row[lo + 1]; i < i1; ++i) {
-    const int64_t h = col[i];
-    if (12 * h >= best) continue;
-    int32_t n[8];
-    load_hex(hex, h, n);
-    for (int kk = 0; kk < 12; ++kk) {
-      const int32_t x = n[kEdge[kk][0]], y = n[kEdge[kk][1]];
-      if ((x == lo && y == hi) || (x == hi && y == lo)) {
-        best = 12 * h + kk < best ? 12 * h + kk : best;
-        break;
-      }
-    }
-  }
+  // the first hex holding the edge; hex e itself holds it, so one is found
+  const int64_t c = common_edge(row, col, a, b);
+  const int64_t best = c >= 0 && c < t ? c : t;
   own[t] = (int32_t)best;
   flag[t] = best == t ? 1 : 0;
 }
@@ -122,27 +203,11 @@ __global__ void k_face_owner(const int32_t *hex, int64_t nh, const int32_t *row,
   if (t >= 6 * nh) return;
   const int64_t e = t / 6;
   const int f = (int)(t - 6 * e);
-  int32_t s[4];
+  int32_t q[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) s[a] = hex[8 * e + kFace[f][a]];
-  sort4(s);
-  int64_t best = t;
-  for (int32_t i = row[s[0]], i1 = row[s[0] + 1]; i < i1; ++i) {
-    const int64_t h = col[i];
-    if (6 * h >= best) continue;
-    int32_t n[8];
-    load_hex(hex, h, n);
-    for (int ff = 0; ff < 6; ++ff) {
-      int32_t q[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) q[a] = n[kFace[ff][a]];
-      sort4(q);
-      if (q[0] == s[0] && q[1] == s[1] && q[2] == s[2] && q[3] == s[3]) {
-        best = 6 * h + ff < best ? 6 * h + ff : best;
-        break;
-      }
-    }
-  }
+  for (int a = 0; a < 4; ++a) q[a] = hex[8 * e + kFace[f][a]];
+  const int64_t c = common_face(hex, row, col, q);
+  const int64_t best = c >= 0 && c < t ? c : t;
   own[t] = (int32_t)best;
   flag[t] = best == t ? 1 : 0;
 }
@@ -337,40 +402,17 @@ __global__ void k_hex_children(const int32_t *hex, const int8_t *ply, int64_t nh
   }
 }
 
-// node id of the divided edge {a, b} or face {q0..q3} of the mesh: found in
-// a hex around the smallest node; -1 when no hex has it
-__device__ int32_t find_edge(const int32_t *hex, const int32_t *row, const int32_t *col, const int32_t *eown,
-                             const int32_t *eidx, int64_t nn, int32_t a, int32_t b) {
-  const int32_t lo = a < b ? a : b, hi = a < b ? b : a;
-  for (int32_t i = row[lo], i1 = row[lo + 1]; i < i1; ++i) {
-    const int64_t h = col[i];
-    int32_t n[8];
-    load_hex(hex, h, n);
-    for (int kk = 0; kk < 12; ++kk) {
-      const int32_t x = n[kEdge[kk][0]], y = n[kEdge[kk][1]];
-      if ((x == lo && y == hi) || (x == hi && y == lo)) return (int32_t)(nn + eidx[eown[12 * h + kk]]);
-    }
-  }
-  return -1;
+// node id of the divided edge {a, b} or face {q0..q3} (q0, q2 opposite) of
+// the mesh, from the first hex that has it; -1 when no hex has it
+__device__ int32_t find_edge(const int32_t *row, const int32_t *col, const int32_t *eown, const int32_t *eidx,
+                             int64_t nn, int32_t a, int32_t b) {
+  const int64_t c = common_edge(row, col, a, b);
+  return c < 0 ? -1 : (int32_t)(nn + eidx[eown[c]]);
 }
 __device__ int32_t find_face(const int32_t *hex, const int32_t *row, const int32_t *col, const int32_t *fown,
                              const int32_t *fidx, int64_t nn, int64_t ne, const int32_t q[4]) {
-  int32_t s[4] = {q[0], q[1], q[2], q[3]};
-  sort4(s);
-  for (int32_t i = row[s[0]], i1 = row[s[0] + 1]; i < i1; ++i) {
-    const int64_t h = col[i];
-    int32_t n[8];
-    load_hex(hex, h, n);
-    for (int ff = 0; ff < 6; ++ff) {
-      int32_t v[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) v[a] = n[kFace[ff][a]];
-      sort4(v);
-      if (v[0] == s[0] && v[1] == s[1] && v[2] == s[2] && v[3] == s[3])
-        return (int32_t)(nn + ne + fidx[fown[6 * h + ff]]);
-    }
-  }
-  return -1;
+  const int64_t c = common_face(hex, row, col, q);
+  return c < 0 ? -1 : (int32_t)(nn + ne + fidx[fown[c]]);
 }
 
 // the 4 children of an interface element: both faces divided as hex faces
@@ -392,7 +434,7 @@ __global__ void k_coh_children(const int32_t *coh, int64_t nc, const int32_t *he
     for (int a = 0; a < 4; ++a) {
       L[s][qx[a] + 3 * qy[a]] = q[a];
       const int b = (a + 1) & 3;
-      const int32_t id = find_edge(hex, row, col, eown, eidx, nn, q[a], q[b]);
+      const int32_t id = find_edge(row, col, eown, eidx, nn, q[a], q[b]);
       ok = ok && id >= 0;
       L[s][(qx[a] + qx[b]) / 2 + 3 * ((qy[a] + qy[b]) / 2)] = id;
     }
@@ -500,6 +542,8 @@ int divide(pdn_refined *r, Level &in, cudaStream_t s) {
   chk(scan<int32_t>(deg, nn, row, temp, s));
   chk(cudaMemcpyAsync(cursor, row, sizeof(int32_t) * nn, cudaMemcpyDeviceToDevice, s));
   k_fill<<<grid_of(8 * nh, B), B, 0, s>>>(in.hex, 8 * nh, cursor, col);
+  chk(cudaGetLastError());
+  k_sort_rows<<<grid_of(nn, B), B, 0, s>>>(row, nn, col);
   chk(cudaGetLastError());
   k_edge_owner<<<grid_of(12 * nh, B), B, 0, s>>>(in.hex, nh, row, col, eown, eflag);
   chk(cudaGetLastError());
