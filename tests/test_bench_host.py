@@ -1,0 +1,82 @@
+"""Host-side parts of bench.py that decide whether a bench line is accepted:
+the clock record taken during the timed region (median SM clock, maximum,
+throttle reasons) and the algorithmic-byte counts behind the roofline
+fractions.  No GPU is used."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _sampler_with(lines):
+    s = bench.ClockSampler(0)
+    fd, s.path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    return s
+
+
+def test_clock_summary_median_maximum_and_reasons():
+    # index, sm, max sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    s = _sampler_with([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ])
+    out = s.summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+    assert not os.path.exists(s.path)
+
+
+def test_clock_summary_flags_thermal_slowdown():
+    s = _sampler_with(["0, 1500, 2070, 800, 0x20, Not Active, Active, Active, Not Active"])
+    out = s.summary()
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_thermal_slowdown"]
+    assert out["sm_mhz"] == 1500.0
+
+
+def test_clock_summary_without_samples():
+    s = _sampler_with([])
+    assert s.summary()["reasons"] == ["unsampled"]
+    s2 = bench.ClockSampler(0)
+    assert s2.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+
+def test_algorithmic_bytes_of_the_benchmark_plate():
+    """The 100x150x4.4 mm plate (393,216 hexes, 344,064 interfaces, 771,807
+    nodes, 24,897 surface nodes): per hex 32 B connectivity + 1 B ply + 448 B
+    of history read and written, per node 24 B; a whole step as stated in
+    bench.step_alg_bytes."""
+    assert bench.hex_alg_bytes(393216, 771807) == 393216 * 481 + 771807 * 24 == 207660264
+    assert bench.coh_alg_bytes(344064) == 344064 * 64
+    assert bench.step_alg_bytes(393216, 344064, 771807, 24897) == (
+        393216 * 481 + 344064 * 64 + 771807 * 141 + 24897 * 48)
+
+
+def test_algorithmic_bytes_of_one_division():
+    """The AS4/8552 coupon divided once: coarse mesh read once, divided mesh
+    written once (25 B per node, 33 B per hex, 32 B per interface, 4 B per
+    surface node)."""
+    coarse = (433680, 228528, 171396, 28912)
+    nn1, ns1 = 2643965, 114955
+    got = bench.mmu_alg_bytes(*coarse, nn1, ns1)
+    want = (433680 * 25 + 228528 * 33 + 171396 * 32 + 28912 * 4) + (
+        nn1 * 25 + 8 * 228528 * 33 + 4 * 171396 * 32 + ns1 * 4)
+    assert got == want == 172812769
+
+
+def test_bench_help_runs_without_a_gpu():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0 and "--workload" in r.stdout
