@@ -99,6 +99,17 @@ def test_fp64_damage_and_interfaces_from_seeded_state(pkg):
         assert np.abs(got - exp[:, :, k].max(axis=1)).max() < 1e-6
     got = pkg.pdn_damage_field(g.ctx, "DCOH")
     assert np.abs(got - rD.max(axis=1)).max() < 1e-6
+    # equivalent plastic shear strain: element maximum of the last history field
+    got = pkg.pdn_damage_field(g.ctx, "PLASTIC")
+    want = hist[:, :, 6].max(axis=1)
+    assert want.max() > 0.0
+    assert np.abs(got - want).max() <= 1e-6 * want.max()
+    # the device-pointer output gives the same floats
+    import torch
+    dev = torch.zeros(w.plate.n_hex, dtype=torch.float32, device="cuda")
+    pkg.pdn_damage_field(g.ctx, "D2", out=dev)
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), pkg.pdn_damage_field(g.ctx, "D2"))
 
 
 def test_fp32_damage_from_seeded_state(pkg):
