@@ -174,6 +174,32 @@ def test_csr_slots_when_a_node_has_more_than_eight_elements(pkg):
     assert _rel(dg, do) < F64_TOL
 
 
+def test_profiled_steps_are_the_same_steps(pkg):
+    """pdn_profile_kernels advances real steps, launching each kernel on its
+    own between CUDA events (no graph, the interface kernel on the same
+    stream): from the same damaging state, 30 stepped + 30 profiled steps end
+    bitwise where 60 stepped steps end (FP64: no tuned variant involved), and
+    every kernel reports a positive mean time and at least one launch per
+    profiled step."""
+    w = _damage_plate(fp64=True)
+    st = _damaging_state(w)
+    a, b = pkg.Solver(w), pkg.Solver(w)
+    for g in (a, b):
+        pkg.pdn_set_state(g.ctx, *st)
+    a.step(60)
+    b.step(30)
+    prof = pkg.pdn_profile_kernels(b.ctx, 30)
+    (da, va, _), (db, vb, _) = a.state(), b.state()
+    assert np.array_equal(da, db) and np.array_equal(va, vb)
+    assert np.array_equal(a.force_history(), b.force_history())
+    assert a.info()["step"] == b.info()["step"]
+    for k in pkg.KERNELS:
+        ms, n = prof[k]
+        assert n >= 30 and ms > 0.0, (k, ms, n)
+    a.close()
+    b.close()
+
+
 def test_internal_force_matches_oracle(pkg):
     # FP32: nodal forces are sums of element contributions that largely cancel,
     # so the FP32 error relative to the largest nodal force is ~1e-5..1e-4
