@@ -368,7 +368,14 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
     std::vector<std::thread> th;
     for (int t = 0; t < nt; ++t) {
       const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
-      if (b < e) th.emplace_back([&, b, e, t]() { body(b, e, t); });
+      if (b >= e) continue;
+      // a chunk whose thread cannot be started runs here (no exception may
+      // leave the library)
+      try {
+        th.emplace_back([&, b, e, t]() { body(b, e, t); });
+      } catch (...) {
+        body(b, e, t);
+      }
     }
     for (auto &x : th) x.join();
   };
