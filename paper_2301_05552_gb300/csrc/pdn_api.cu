@@ -287,7 +287,8 @@ void pdn_destroy(pdn_ctx *ctx) {
   delete ctx;
 }
 
-int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat, const pdn_options *opt) {
+static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat,
+                              const pdn_options *opt) {
   g_init_error.clear();
   if (!out) {
     g_init_error = "out is NULL";
@@ -791,6 +792,19 @@ int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *
   return PDN_OK;
 }
 
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_init_mesh(pdn_ctx **out, const pdn_mesh_desc *mesh, const pdn_material *mat, const pdn_options *opt) {
+  try {
+    return pdn_init_mesh_body(out, mesh, mat, opt);
+  } catch (const std::bad_alloc &) {
+    g_init_error = "host allocation failed";
+    return PDN_E_OOM;
+  } catch (...) {
+    g_init_error = "unexpected host error";
+    return PDN_E_ARG;
+  }
+}
+
 int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double centre[3], const double velocity[3]) {
   if (!ctx) return PDN_E_ARG;
   if (!centre || !velocity || !(radius > 0) || !(mass > 0)) return fail(ctx, PDN_E_ARG, "radius and mass must be positive");
@@ -1002,7 +1016,7 @@ int pdn_get_state(pdn_ctx *ctx, double *d, double *v, double *imp) {
   return PDN_OK;
 }
 
-int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v) {
+static int pdn_set_state_body(pdn_ctx *ctx, const double *d, const double *v) {
   if (!ctx) return PDN_E_ARG;
   if (!d || !v) return fail(ctx, PDN_E_ARG, "d and v are required");
   int rc = read_ctl(ctx);
@@ -1032,7 +1046,18 @@ int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v) {
   return prime_state(ctx);
 }
 
-int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v) {
+  try {
+    return pdn_set_state_body(ctx, d, v);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
+}
+
+static int pdn_get_contact_body(pdn_ctx *ctx, uint8_t *active, double *lambda) {
   if (!ctx) return PDN_E_ARG;
   int rc = read_ctl(ctx);
   if (rc) return rc;
@@ -1050,6 +1075,17 @@ int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {
       if (!a[s]) lambda[s] = 0.0;
   }
   return PDN_OK;
+}
+
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {
+  try {
+    return pdn_get_contact_body(ctx, active, lambda);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
 }
 
 int pdn_internal_force(pdn_ctx *ctx, double *f_int) {

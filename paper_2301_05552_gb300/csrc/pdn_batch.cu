@@ -729,7 +729,7 @@ void pdn_batch_destroy(pdn_batch *b) {
   delete b;
 }
 
-int pdn_batch_init(pdn_batch **out, int32_t n_plates, const pdn_mesh_desc *meshes, const pdn_material *mats,
+static int pdn_batch_init_body(pdn_batch **out, int32_t n_plates, const pdn_mesh_desc *meshes, const pdn_material *mats,
                    const pdn_options *opt) {
   g_batch_init_error.clear();
   if (!out) {
@@ -783,6 +783,18 @@ int pdn_batch_init(pdn_batch **out, int32_t n_plates, const pdn_mesh_desc *meshe
   cudaMemset(b->d_sync, 0, sizeof(BatchSync));
   *out = b;
   return PDN_OK;
+}
+
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_batch_init(pdn_batch **out, int32_t n_plates, const pdn_mesh_desc *meshes, const pdn_material *mats,
+                   const pdn_options *opt) {
+  try {
+    return pdn_batch_init_body(out, n_plates, meshes, mats, opt);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
 }
 
 pdn_ctx *pdn_batch_plate(pdn_batch *b, int32_t p) {

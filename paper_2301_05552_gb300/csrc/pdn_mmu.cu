@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -657,7 +658,7 @@ int divide(pdn_refined *r, Level &in, cudaStream_t s) {
 
 using namespace pdn;
 
-extern "C" int pdn_mesh_multiply(pdn_refined **out, const pdn_mesh_desc *m, int32_t ndivi, void *stream) {
+static int pdn_mesh_multiply_body(pdn_refined **out, const pdn_mesh_desc *m, int32_t ndivi, void *stream) {
   if (!out) return PDN_E_ARG;
   *out = nullptr;
   auto bad = [](int code, const std::string &msg) {
@@ -758,6 +759,19 @@ extern "C" int pdn_mesh_multiply(pdn_refined **out, const pdn_mesh_desc *m, int3
   return PDN_OK;
 }
 
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+extern "C" int pdn_mesh_multiply(pdn_refined **out, const pdn_mesh_desc *m, int32_t ndivi, void *stream) {
+  try {
+    return pdn_mesh_multiply_body(out, m, ndivi, stream);
+  } catch (const std::bad_alloc &) {
+    g_mmu_error = "host allocation failed";
+    return PDN_E_OOM;
+  } catch (...) {
+    g_mmu_error = "unexpected host error";
+    return PDN_E_ARG;
+  }
+}
+
 extern "C" int pdn_refined_get_info(const pdn_refined *r, pdn_refined_info *info) {
   if (!r || !info) return PDN_E_ARG;
   std::memset(info, 0, sizeof(*info));
@@ -792,7 +806,7 @@ extern "C" int pdn_refined_get(const pdn_refined *r, double *X, int32_t *hex, in
   return PDN_OK;
 }
 
-extern "C" int pdn_init_refined(pdn_ctx **out, const pdn_refined *r, const pdn_material *mat,
+static int pdn_init_refined_body(pdn_ctx **out, const pdn_refined *r, const pdn_material *mat,
                                 const pdn_options *opt) {
   if (!out || !r) return PDN_E_ARG;
   *out = nullptr;
@@ -816,6 +830,18 @@ extern "C" int pdn_init_refined(pdn_ctx **out, const pdn_refined *r, const pdn_m
   d.fixed = fixed.data();
   d.surf = r->ns ? surf.data() : nullptr;
   return pdn_init_mesh(out, &d, mat, opt);
+}
+
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+extern "C" int pdn_init_refined(pdn_ctx **out, const pdn_refined *r, const pdn_material *mat,
+                                const pdn_options *opt) {
+  try {
+    return pdn_init_refined_body(out, r, mat, opt);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
 }
 
 extern "C" void pdn_refined_destroy(pdn_refined *r) {

@@ -778,7 +778,7 @@ void pdn_sur_destroy(pdn_surrogate *s) {
   delete s;
 }
 
-int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint64_t seed, void *stream) {
+static int pdn_sur_create_body(pdn_surrogate **out, const pdn_material *mat, double lc, uint64_t seed, void *stream) {
   g_sur_error.clear();
   if (!out) {
     g_sur_error = "out is NULL";
@@ -846,7 +846,18 @@ int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint
   return PDN_OK;
 }
 
-int pdn_sur_generate(pdn_surrogate *s, int64_t n_paths, int32_t steps, double strain_max, double cyclic_fraction,
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_sur_create(pdn_surrogate **out, const pdn_material *mat, double lc, uint64_t seed, void *stream) {
+  try {
+    return pdn_sur_create_body(out, mat, lc, seed, stream);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
+}
+
+static int pdn_sur_generate_body(pdn_surrogate *s, int64_t n_paths, int32_t steps, double strain_max, double cyclic_fraction,
                      double onset_ratio, uint64_t seed, int64_t *n_kept) {
   if (!s) return PDN_E_ARG;
   if (n_paths < 1 || steps < 1 || steps > 1024 || !(strain_max > 0.0) || !(onset_ratio > 0.0) ||
@@ -935,6 +946,18 @@ int pdn_sur_generate(pdn_surrogate *s, int64_t n_paths, int32_t steps, double st
   s->sc = sc;
   if (n_kept) *n_kept = tot;
   return PDN_OK;
+}
+
+// No exception leaves the library: a failed host allocation is PDN_E_OOM.
+int pdn_sur_generate(pdn_surrogate *s, int64_t n_paths, int32_t steps, double strain_max, double cyclic_fraction,
+                     double onset_ratio, uint64_t seed, int64_t *n_kept) {
+  try {
+    return pdn_sur_generate_body(s, n_paths, steps, strain_max, cyclic_fraction, onset_ratio, seed, n_kept);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
 }
 
 int pdn_sur_get_data(pdn_surrogate *s, int64_t offset, int64_t n, float *x, float *y) {
