@@ -203,8 +203,11 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
  * released nodes and the nodes of those elements (everything else has the
  * same inputs as before and keeps its values); the environment variable
  * PDN_FULL_REPEAT=1, read by pdn_init_mesh, makes repetitions evaluate every
- * element and node, with the same results.  Returns after the work has
- * completed on the stream.
+ * element and node, with the same results.  The kernels of a pass are
+ * launched with programmatic dependent launch (each waits for the previous
+ * grid before reading); PDN_PDL=0, read once per process, launches them
+ * plainly, with the same results.  Returns after the work has completed on
+ * the stream.
  * Errors: PDN_E_STATE without a striker, PDN_E_NONFINITE,
  * PDN_E_RELEASE_LIMIT (both sticky), PDN_E_CUDA. */
 int pdn_step(pdn_ctx *ctx, int64_t nsteps);
