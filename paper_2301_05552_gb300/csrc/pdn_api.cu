@@ -322,6 +322,10 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     if (surf_of[j] >= 0) return bad("duplicate surface node id");
     surf_of[j] = (int32_t)s;
   }
+  // a contact surface numbered as one ascending run of node ids
+  int32_t surf_base = ns > 0 ? mesh->surf[0] : -1;
+  for (int64_t s = 1; s < ns && surf_base >= 0; ++s)
+    if (mesh->surf[s] != mesh->surf[0] + s) surf_base = -1;
   for (int64_t c = 0; c < nc; ++c)
     for (int a = 0; a < 4; ++a)
       for (int i = 0; i < 3; ++i)
@@ -777,6 +781,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     D.all_boxes = all_boxes ? 1 : 0;
     D.all_flat_coh = all_flat_coh ? 1 : 0;
     D.ell = ell ? 1 : 0;
+    D.surf_base = surf_base;
   };
   if (fp64)
     wire(ctx->Dd, double{});

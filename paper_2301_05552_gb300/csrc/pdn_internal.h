@@ -172,7 +172,10 @@ struct Dev {
   // inputs leave the training box) take the exact law
   const float *sur_params;
   float sur_ratio2;
-  int32_t sur_pad;
+  // the first node id when the contact surface is the ascending contiguous
+  // range surf[s] = surf_base + s (then s and j convert without the index
+  // arrays), else -1
+  int32_t surf_base;
 };
 
 // Launchers (pdn_kernels.cu).

@@ -49,7 +49,7 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
   const Striker *S = D.imp;
   const StrikerStep *ss = D.imp_step;
   const int64_t nn = D.nn, ns = D.ns;
-  const int64_t j = D.surf[s];
+  const int64_t j = D.surf_base >= 0 ? D.surf_base + s : D.surf[s];
   const int cur = ctl->dpar;
   const int spar = (int)((ctl->step + 1) & 1), ppar = (int)(ctl->step & 1);
   double *d = D.d[cur];
@@ -74,10 +74,15 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
       near = dx * dx + dy * dy + dz * dz < rr * rr;
     }
     if (near && S->has && (fl & 7) != 7) {
-      double x[3], r2 = 0.0;
+      // every load of the node and the striker is issued before the first
+      // store (a store to the trial copy could alias them otherwise)
+      double x[3], r2 = 0.0, dj[3], vj[3], w[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        x[i] = D.Xs[i * ns + s] + d[i * nn + j] - ss->c[i];
+        dj[i] = d[i * nn + j];
+        vj[i] = v[i * nn + j];
+        w[i] = ss->w[i];
+        x[i] = D.Xs[i * ns + s] + dj[i] - ss->c[i];
         r2 += x[i] * x[i];
       }
       const double r = sqrt(r2);
@@ -86,15 +91,13 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
         a = 1;
         const double ir = 1.0 / r;
         double n[3] = {x[0] * ir, x[1] * ir, x[2] * ir};
-        double dj[3], vj[3], vn = 0.0, wn = 0.0;
+        double vn = 0.0, wn = 0.0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          dj[i] = d[i * nn + j];
-          vj[i] = v[i * nn + j];
           D.trial[i * ns + s] = dj[i];
           D.trial[(3 + i) * ns + s] = vj[i];
           vn += vj[i] * n[i];
-          wn += ss->w[i] * n[i];
+          wn += w[i] * n[i];
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -769,6 +772,15 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
 // repetition when adhesive nodes were released (Algorithm 2: the MPI_MAX of
 // kfl_reset becomes this single-block decision), or halts.  On commit it also
 // advances the striker for the next pass (RK4 with the committed force).
+// The 0/1 flag bytes of 16 consecutive surface nodes as a 16-bit mask, bit b
+// for node b: per 32-bit part, the multiply moves the low bits of its four
+// bytes (0, 8, 16, 24) to bits 21..24 with no two partial products on the
+// same bit, so there is no carry.
+__device__ __forceinline__ uint32_t flag_mask16(uint4 q) {
+  const auto four = [](uint32_t x) { return (((x & 0x01010101u) * 0x00204081u) >> 21) & 0xFu; };
+  return four(q.x) | (four(q.y) << 4) | (four(q.z) << 8) | (four(q.w) << 12);
+}
+
 template <typename T>
 __device__ void tail_block(const Dev<T> &D, int mode) {
   Ctl *ctl = D.ctl;
@@ -819,6 +831,7 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
       const int64_t w0 = (int64_t)v * per;
       const int64_t w1 = w0 + per < words ? w0 + per : words;
       int cnt = 0;
+#pragma unroll 4
       for (int64_t wi = w0; wi < w1; ++wi) {
         const uint4 q = aw[wi];
         cnt += __popc(q.x & 0x01010101u) + __popc(q.y & 0x01010101u) + __popc(q.z & 0x01010101u) +
@@ -855,12 +868,9 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
         const int64_t w0 = (int64_t)v * per;
         const int64_t w1 = w0 + per < words ? w0 + per : words;
         int o = s_off[v];
+#pragma unroll 4
         for (int64_t wi = w0; wi < w1; ++wi) {
-          const uint4 q = aw[wi];
-          if ((q.x | q.y | q.z | q.w) == 0u) continue;
-          const uint32_t part[4] = {q.x, q.y, q.z, q.w};
-          for (int b = 0; b < 16; ++b)
-            if ((part[b >> 2] >> (8 * (b & 3))) & 1u) s_list[o++] = (int)(wi * 16 + b);
+          for (uint32_t m = flag_mask16(aw[wi]); m != 0u; m &= m - 1u) s_list[o++] = (int)(wi * 16 + __ffs(m) - 1);
         }
       }
       __syncthreads();
@@ -871,28 +881,40 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     double f0 = 0.0, f1 = 0.0, f2 = 0.0;
     int nact = 0, nadh = 0;
     if (stepping && total <= kTailCap) {
-      for (int i = v; i < total; i += kTailLanes) {
-        const int64_t s = s_list[i];
-        const double lam = D.lam[s];
-        if (lam < 0.0) {
-          ++nadh;
-        } else {
-          ++nact;
-          f0 += lam * D.nrm[s];
-          f1 += lam * D.nrm[ns + s];
-          f2 += lam * D.nrm[2 * ns + s];
+      // the lane's entries in list order, kTailBatch at a time: every load of
+      // a batch (lambda and the normal of each entry) is issued before any
+      // is used, so a batch costs one round of memory latency
+      constexpr int kTailBatch = 4;
+      for (int i0 = v; i0 < total; i0 += kTailBatch * kTailLanes) {
+        double lam[kTailBatch], n0[kTailBatch], n1[kTailBatch], n2[kTailBatch];
+#pragma unroll
+        for (int u = 0; u < kTailBatch; ++u) {
+          const int i = i0 + u * kTailLanes;
+          const int64_t s = i < total ? s_list[i] : 0;
+          lam[u] = i < total ? D.lam[s] : 0.0;
+          n0[u] = i < total ? D.nrm[s] : 0.0;
+          n1[u] = i < total ? D.nrm[ns + s] : 0.0;
+          n2[u] = i < total ? D.nrm[2 * ns + s] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kTailBatch; ++u) {
+          if (i0 + u * kTailLanes >= total) break;
+          if (lam[u] < 0.0) {
+            ++nadh;
+          } else {
+            ++nact;
+            f0 += lam[u] * n0[u];
+            f1 += lam[u] * n1[u];
+            f2 += lam[u] * n2[u];
+          }
         }
       }
     } else if (stepping) {
       const int64_t w0 = (int64_t)v * per;
       const int64_t w1 = w0 + per < words ? w0 + per : words;
       for (int64_t wi = w0; wi < w1; ++wi) {
-        const uint4 q = aw[wi];
-        if ((q.x | q.y | q.z | q.w) == 0u) continue;
-        const uint32_t part[4] = {q.x, q.y, q.z, q.w};
-        for (int b = 0; b < 16; ++b) {
-          if (!((part[b >> 2] >> (8 * (b & 3))) & 1u)) continue;
-          const int64_t s = wi * 16 + b;
+        for (uint32_t m = flag_mask16(aw[wi]); m != 0u; m &= m - 1u) {
+          const int64_t s = wi * 16 + __ffs(m) - 1;
           const double lam = D.lam[s];
           if (lam < 0.0) {
             ++nadh;
@@ -1064,16 +1086,20 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
   double a[3];
   bool done = false;
   if ((fl & 8) && mode != MODE_PRIME) {
-    const int64_t s = D.surf_of[j];
+    const int64_t s = D.surf_base >= 0 ? j - D.surf_base : D.surf_of[j];
     const int spar = (int)((ctl->step + 1) & 1);
-    if (D.act[spar][s]) {
-      const int64_t ns = D.ns;
-      const double m = D.mass[j];
-      const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
+    // the contact flag, the normal, the mass and the striker's acceleration
+    // in one round of loads (the normal of an inactive node is not used)
+    const int64_t ns = D.ns;
+    const bool on = D.act[spar][s] != 0;
+    const double m = D.mass[j];
+    const double n[3] = {D.nrm[s], D.nrm[ns + s], D.nrm[2 * ns + s]};
+    const StrikerStep *ss = D.imp_step;
+    const double aI[3] = {ss->aI[0], ss->aI[1], ss->aI[2]};
+    if (on) {
       const double fr[3] = {m * D.grav[0] - (double)fx, m * D.grav[1] - (double)fy, m * D.grav[2] - (double)fz};
-      const StrikerStep *ss = D.imp_step;
       const double fdot = fr[0] * n[0] + fr[1] * n[1] + fr[2] * n[2];
-      const double adot = ss->aI[0] * n[0] + ss->aI[1] * n[1] + ss->aI[2] * n[2];
+      const double adot = aI[0] * n[0] + aI[1] * n[1] + aI[2] * n[2];
       const double lam = m * adot - fdot;
       D.lam[s] = lam;
       if (lam < 0.0) {

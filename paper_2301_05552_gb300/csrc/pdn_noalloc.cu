@@ -108,6 +108,7 @@ cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32
   D.nh = nh;
   D.nc = 0;
   D.ns = 0;
+  D.surf_base = -1;
   D.hex = hex;
   D.coh = nullptr;
   D.ply = ply;

@@ -80,3 +80,17 @@ def test_bench_help_runs_without_a_gpu():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 0 and "--workload" in r.stdout
+
+
+def test_traffic_record_hash_covers_the_hex_kernel_only():
+    """The stored k_hex DRAM-traffic record is keyed by a hash of the source
+    k_hex is compiled from: the element sections of the item bodies count,
+    the contact, interface, tail and gather sections do not."""
+    with open(os.path.join(ROOT, "paper_2301_05552_gb300", "csrc", "pdn_items.cuh"), encoding="utf-8") as f:
+        text = f.read()
+    kept = bench.hex_sections(text)
+    for name in ("element_slots", "hex_box_pairs_core", "hex_item_box_pairs", "hex_item("):
+        assert name in kept
+    for name in ("contact_item", "coh_item", "tail_block", "gather_item"):
+        assert name in text and name not in kept
+    assert len(bench.kernel_source_hash()) == 16
