@@ -381,6 +381,11 @@ def run_gpu(args, ws, rank, local):
         rate, n, dt = oracle_rate(w, args.cpu_seconds, 10 ** 6, cores)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"{n} explicit steps of the same workload from rest ({dt:.1f} s)"}
+        # the same oracle on one thread, on a third of the time budget
+        r1, n1, dt1 = oracle_rate(w, max(3.0, args.cpu_seconds / 3.0), 10 ** 6, 1)
+        line["cpu_baseline"]["single_thread"] = {
+            "value": r1, "unit": UNIT, "cores": 1,
+            "sample": f"{n1} explicit steps of the same workload from rest ({dt1:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
