@@ -545,7 +545,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   const bool fp64 = ctx->precision == PDN_FP64;
   const size_t ts = fp64 ? 8 : 4;
   struct Ptrs {
-    int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos;
+    int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos, *act_cnt;
     uint32_t *rank;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
@@ -586,6 +586,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     }
     P.fe = A.take<char>(ts * 4 * n_slots);
     P.rel = A.take<uint8_t>(ns1);
+    P.act_cnt = A.take<int32_t>(sizeof(int32_t) * ((ns1 + kActRun - 1) / kActRun));
     P.rmark_e = A.take<uint8_t>(nh + nc);
     P.rmark_n = A.take<uint8_t>(nn);
     P.nrm = A.take<double>(sizeof(double) * 3 * ns1);
@@ -757,6 +758,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     }
     D.fe = reinterpret_cast<V4 *>(d_fe);
     D.rel = d_rel;
+    D.act_cnt = P.act_cnt;
     // PDN_FULL_REPEAT=1: repeated passes evaluate every element and node
     // again (the reference for the local repetition, same results)
     const char *fr = std::getenv("PDN_FULL_REPEAT");

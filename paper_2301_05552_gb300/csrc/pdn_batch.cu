@@ -681,6 +681,7 @@ int upload_records(pdn_batch *b) {
   std::vector<Mat<T>> M(b->n);
   for (int p = 0; p < b->n; ++p) {
     D[p] = dev_of<T>(b->plates[p]);
+    D[p].act_cnt = nullptr;  // the batch's contact tiles do not count: its tails scan the flags
     M[p] = mat_of<T>(b->plates[p]);
   }
   PB_CU(cudaMalloc(&b->d_dev, sizeof(Dev<T>) * b->n), "plate records");

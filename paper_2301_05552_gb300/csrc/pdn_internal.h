@@ -7,6 +7,10 @@
 
 namespace pdn {
 
+// Contact-surface nodes per block of the contact kernel, and per run of the
+// active-node counts it writes (Dev::act_cnt): 16 flag words of 16 nodes.
+constexpr int kActRun = 256;
+
 // Device-side state machine of a pass.  A pass is one launch of the five step
 // kernels (contact, hex, interface, gather, tail); the tail decides whether
 // the next pass advances to a new step or repeats the current one after
@@ -131,6 +135,10 @@ struct Dev {
   // contact
   uint8_t *act[2];         // [ns] contact set by step parity
   uint8_t *rel;            // [ns] released in the current step
+  // active contact nodes of each run of kActRun consecutive surface nodes,
+  // written by the contact kernel of every stepping pass and read by the
+  // tail of the same pass (null: the tail counts the flag words itself)
+  int32_t *act_cnt;        // [ceil(ns / kActRun)]
   // local repetition of a step: marks of the elements ([nh + nc], hexes then
   // interfaces) and nodes ([nn]) that a repeated pass evaluates again; zero
   // outside a repeated pass (null: repeated passes evaluate everything)

@@ -41,11 +41,12 @@ __device__ __forceinline__ void element_slots(const Dev<T> &D, const int32_t *co
 // computed (its RK4 update with the committed contact force held over the
 // step, Eq. rk4) was produced by the tail of the previous pass, or by
 // k_striker_init after pdn_set_impactor; this kernel only reads it.
+// Returns whether node s is in the contact set when the item is done.
 template <typename T>
-__device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mode) {
+__device__ __forceinline__ bool contact_item(const Dev<T> &D, int64_t s, int mode) {
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
-  if (s >= D.ns) return;
+  if (s >= D.ns) return false;
   const Striker *S = D.imp;
   const StrikerStep *ss = D.imp_step;
   const int64_t nn = D.nn, ns = D.ns;
@@ -118,8 +119,10 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
       }
     }
     D.act[spar][s] = a;
+    return a != 0;
   } else {  // MODE_REPEAT: restore the released nodes to their trial state
-    if (D.rel[s] && D.act[spar][s]) {
+    const bool on = D.act[spar][s] != 0;
+    if (D.rel[s] && on) {
       double dj[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -137,7 +140,9 @@ __device__ __forceinline__ void contact_item(const Dev<T> &D, int64_t s, int mod
       // the elements of the released node are evaluated again
       if (D.rmark_e != nullptr)
         for (int k = D.row[j], k1 = D.row[j + 1]; k < k1; ++k) D.rmark_e[D.col[k] >> 3] = 1;
+      return false;
     }
+    return on;
   }
 }
 
@@ -825,7 +830,89 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
   // and hold 0 or 1 per node
   const uint4 *aw = stepping ? reinterpret_cast<const uint4 *>(D.act[(int)((ctl->step + 1) & 1)]) : nullptr;
   int total = 0;
-  if (stepping) {
+  // With the contact kernel's counts per run of kActRun surface nodes, the
+  // list is built from them: an exclusive prefix over the runs, then the
+  // warps take the non-empty runs and read a run's 16 flag words with one
+  // load per lane of a half-warp, writing the run's nodes in surface order
+  // from the run's offset.  The list is the same as the one the flag
+  // words alone give (below); only fewer words are read, and in fewer rounds.
+  constexpr int kRunWords = kActRun / 16;
+  constexpr int kRunCap = 2048;
+  static_assert(kRunWords == 16, "a run is one flag word per lane of a half-warp");
+  __shared__ int s_pre[kRunCap + 1];
+  __shared__ int s_wsum[32];
+  const int64_t nrun = (ns + kActRun - 1) / kActRun;
+  if (stepping && D.act_cnt != nullptr && nrun <= kRunCap) {
+    const int nt = (int)blockDim.x, lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+    const int nw = (nt + 31) >> 5;
+    const int64_t pr = (nrun + nt - 1) / nt;
+    const int64_t r0 = (int64_t)threadIdx.x * pr;
+    const int64_t r1 = r0 + pr < nrun ? r0 + pr : nrun;
+    int tsum = 0;
+#pragma unroll 4
+    for (int64_t r = r0; r < r1; ++r) tsum += D.act_cnt[r];
+    int inc = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      const int x = lane < nw ? s_wsum[lane] : 0;
+      int xi = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, xi, o);
+        if (lane >= o) xi += t;
+      }
+      if (lane < nw) s_wsum[lane] = xi - x;
+      if (lane == nw - 1) s_pre[nrun] = xi;
+    }
+    __syncthreads();
+    int run_base = s_wsum[wid] + inc - tsum;
+    for (int64_t r = r0; r < r1; ++r) {
+      s_pre[r] = run_base;
+      run_base += D.act_cnt[r];
+    }
+    __syncthreads();
+    total = s_pre[nrun];
+    if (total <= kTailCap) {
+      // warp wid looks at runs wid, wid + nw, wid + 2 nw, ... (32 per ballot),
+      // so that the runs of one contact patch spread over the warps; each
+      // half-warp reads one non-empty run (one flag word per lane)
+      const int half = lane >> 4, hl = lane & 15;
+      for (int64_t g = 0; wid + (int64_t)nw * 32 * g < nrun; ++g) {
+        const int64_t r = wid + (int64_t)nw * (32 * g + lane);
+        uint32_t todo = __ballot_sync(0xffffffffu, r < nrun && s_pre[r + 1] > s_pre[r]);
+        while (todo != 0u) {
+          const int ka = __ffs(todo) - 1;
+          todo &= todo - 1u;
+          int kb = -1;
+          if (todo != 0u) {
+            kb = __ffs(todo) - 1;
+            todo &= todo - 1u;
+          }
+          const int k = half ? kb : ka;
+          const int64_t rr = wid + (int64_t)nw * (32 * g + (k < 0 ? 0 : k));
+          const int64_t w = rr * kRunWords + hl;
+          const uint32_t m = (k >= 0 && w < words) ? flag_mask16(aw[w]) : 0u;
+          const int c = __popc(m);
+          int ci = c;
+#pragma unroll
+          for (int o = 1; o < 16; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, ci, o, 16);
+            if (hl >= o) ci += t;
+          }
+          int o = (k >= 0 ? s_pre[rr] : 0) + ci - c;
+          for (uint32_t mm = m; mm != 0u; mm &= mm - 1u, ++o)
+            if (o < kTailCap) s_list[o] = (int)(w * 16 + __ffs(mm) - 1);
+        }
+      }
+      __syncthreads();
+    }
+  } else if (stepping) {
     for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
       const int v = v0 + (int)threadIdx.x;
       const int64_t w0 = (int64_t)v * per;
@@ -890,7 +977,8 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
 #pragma unroll
         for (int u = 0; u < kTailBatch; ++u) {
           const int i = i0 + u * kTailLanes;
-          const int64_t s = i < total ? s_list[i] : 0;
+          int64_t s = i < total ? s_list[i] : 0;
+          s = (s >= 0 && s < ns) ? s : 0;  // a list entry is always a surface index
           lam[u] = i < total ? D.lam[s] : 0.0;
           n0[u] = i < total ? D.nrm[s] : 0.0;
           n1[u] = i < total ? D.nrm[ns + s] : 0.0;

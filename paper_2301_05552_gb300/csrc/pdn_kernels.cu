@@ -40,11 +40,14 @@ __device__ __forceinline__ void pdl_enter() {
 // Kernels of a pass (one launch per step part); the per-item bodies are in
 // pdn_items.cuh, shared with the batched persistent kernel.
 template <typename T>
-__global__ void __launch_bounds__(256) k_contact(Dev<T> D) {
+__global__ void __launch_bounds__(kActRun) k_contact(Dev<T> D) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode != MODE_ADVANCE && mode != MODE_REPEAT) return;
-  contact_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
+  const bool on = contact_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
+  // the run's count of active nodes, for the tail's ordered list
+  const int c = __syncthreads_count(on);
+  if (D.act_cnt != nullptr && threadIdx.x == 0) D.act_cnt[blockIdx.x] = c;
 }
 
 template <typename T, bool BOX, int MINB>
@@ -307,7 +310,7 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
   if (mixed) {
     // one launch for both element kinds; the interface event pair is empty
     if (ev) cudaEventRecord(ev[0], s);
-    launch_k(k_contact<T>, grid_of(D.ns, 256), 256, s, D);
+    launch_k(k_contact<T>, grid_of(D.ns, kActRun), kActRun, s, D);
     if (ev) cudaEventRecord(ev[1], s);
     launch_elem(D, M, s);
     if (ev) cudaEventRecord(ev[2], s);
@@ -320,7 +323,7 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
   }
   const bool concurrent = side != nullptr && ev == nullptr && D.nc > 0;
   if (ev) cudaEventRecord(ev[0], s);
-  launch_k(k_contact<T>, grid_of(D.ns, 256), 256, s, D);
+  launch_k(k_contact<T>, grid_of(D.ns, kActRun), kActRun, s, D);
   if (ev) cudaEventRecord(ev[1], s);
   if (concurrent) {
     cudaEventRecord(fork, s);

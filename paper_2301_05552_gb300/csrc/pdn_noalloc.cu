@@ -109,6 +109,7 @@ cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32
   D.nc = 0;
   D.ns = 0;
   D.surf_base = -1;
+  D.act_cnt = nullptr;
   D.hex = hex;
   D.coh = nullptr;
   D.ply = ply;
