@@ -786,7 +786,11 @@ __device__ __forceinline__ uint32_t flag_mask16(uint4 q) {
   return four(q.x) | (four(q.y) << 4) | (four(q.z) << 8) | (four(q.w) << 12);
 }
 
-template <typename T>
+// RUNS: build the list from the contact kernel's per-run counts when the
+// context has them (the per-pass kernel); the batched kernel, whose contact
+// tiles do not count, instantiates the flag-word scan alone and so does not
+// carry the runs' shared arrays.
+template <typename T, bool RUNS = false>
 __device__ void tail_block(const Dev<T> &D, int mode) {
   Ctl *ctl = D.ctl;
   // the control block and the striker are read once, early, into registers;
@@ -836,83 +840,88 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
   // load per lane of a half-warp, writing the run's nodes in surface order
   // from the run's offset.  The list is the same as the one the flag
   // words alone give (below); only fewer words are read, and in fewer rounds.
-  constexpr int kRunWords = kActRun / 16;
-  constexpr int kRunCap = 2048;
-  static_assert(kRunWords == 16, "a run is one flag word per lane of a half-warp");
-  __shared__ int s_pre[kRunCap + 1];
-  __shared__ int s_wsum[32];
-  const int64_t nrun = (ns + kActRun - 1) / kActRun;
-  if (stepping && D.act_cnt != nullptr && nrun <= kRunCap) {
-    const int nt = (int)blockDim.x, lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
-    const int nw = (nt + 31) >> 5;
-    const int64_t pr = (nrun + nt - 1) / nt;
-    const int64_t r0 = (int64_t)threadIdx.x * pr;
-    const int64_t r1 = r0 + pr < nrun ? r0 + pr : nrun;
-    int tsum = 0;
+  bool listed = false;
+  if constexpr (RUNS) {
+    constexpr int kRunWords = kActRun / 16;
+    constexpr int kRunCap = 2048;
+    static_assert(kRunWords == 16, "a run is one flag word per lane of a half-warp");
+    __shared__ int s_pre[kRunCap + 1];
+    __shared__ int s_wsum[32];
+    const int64_t nrun = (ns + kActRun - 1) / kActRun;
+    if (stepping && D.act_cnt != nullptr && nrun <= kRunCap) {
+      listed = true;
+      const int nt = (int)blockDim.x, lane = (int)threadIdx.x & 31, wid = (int)threadIdx.x >> 5;
+      const int nw = (nt + 31) >> 5;
+      const int64_t pr = (nrun + nt - 1) / nt;
+      const int64_t r0 = (int64_t)threadIdx.x * pr;
+      const int64_t r1 = r0 + pr < nrun ? r0 + pr : nrun;
+      int tsum = 0;
 #pragma unroll 4
-    for (int64_t r = r0; r < r1; ++r) tsum += D.act_cnt[r];
-    int inc = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += t;
-    }
-    if (lane == 31) s_wsum[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-      const int x = lane < nw ? s_wsum[lane] : 0;
-      int xi = x;
+      for (int64_t r = r0; r < r1; ++r) tsum += D.act_cnt[r];
+      int inc = tsum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, xi, o);
-        if (lane >= o) xi += t;
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
       }
-      if (lane < nw) s_wsum[lane] = xi - x;
-      if (lane == nw - 1) s_pre[nrun] = xi;
-    }
-    __syncthreads();
-    int run_base = s_wsum[wid] + inc - tsum;
-    for (int64_t r = r0; r < r1; ++r) {
-      s_pre[r] = run_base;
-      run_base += D.act_cnt[r];
-    }
-    __syncthreads();
-    total = s_pre[nrun];
-    if (total <= kTailCap) {
-      // warp wid looks at runs wid, wid + nw, wid + 2 nw, ... (32 per ballot),
-      // so that the runs of one contact patch spread over the warps; each
-      // half-warp reads one non-empty run (one flag word per lane)
-      const int half = lane >> 4, hl = lane & 15;
-      for (int64_t g = 0; wid + (int64_t)nw * 32 * g < nrun; ++g) {
-        const int64_t r = wid + (int64_t)nw * (32 * g + lane);
-        uint32_t todo = __ballot_sync(0xffffffffu, r < nrun && s_pre[r + 1] > s_pre[r]);
-        while (todo != 0u) {
-          const int ka = __ffs(todo) - 1;
-          todo &= todo - 1u;
-          int kb = -1;
-          if (todo != 0u) {
-            kb = __ffs(todo) - 1;
-            todo &= todo - 1u;
-          }
-          const int k = half ? kb : ka;
-          const int64_t rr = wid + (int64_t)nw * (32 * g + (k < 0 ? 0 : k));
-          const int64_t w = rr * kRunWords + hl;
-          const uint32_t m = (k >= 0 && w < words) ? flag_mask16(aw[w]) : 0u;
-          const int c = __popc(m);
-          int ci = c;
+      if (lane == 31) s_wsum[wid] = inc;
+      __syncthreads();
+      if (wid == 0) {
+        const int x = lane < nw ? s_wsum[lane] : 0;
+        int xi = x;
 #pragma unroll
-          for (int o = 1; o < 16; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, ci, o, 16);
-            if (hl >= o) ci += t;
-          }
-          int o = (k >= 0 ? s_pre[rr] : 0) + ci - c;
-          for (uint32_t mm = m; mm != 0u; mm &= mm - 1u, ++o)
-            if (o < kTailCap) s_list[o] = (int)(w * 16 + __ffs(mm) - 1);
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, xi, o);
+          if (lane >= o) xi += t;
         }
+        if (lane < nw) s_wsum[lane] = xi - x;
+        if (lane == nw - 1) s_pre[nrun] = xi;
       }
       __syncthreads();
+      int run_base = s_wsum[wid] + inc - tsum;
+      for (int64_t r = r0; r < r1; ++r) {
+        s_pre[r] = run_base;
+        run_base += D.act_cnt[r];
+      }
+      __syncthreads();
+      total = s_pre[nrun];
+      if (total <= kTailCap) {
+        // warp wid looks at runs wid, wid + nw, wid + 2 nw, ... (32 per ballot),
+        // so that the runs of one contact patch spread over the warps; each
+        // half-warp reads one non-empty run (one flag word per lane)
+        const int half = lane >> 4, hl = lane & 15;
+        for (int64_t g = 0; wid + (int64_t)nw * 32 * g < nrun; ++g) {
+          const int64_t r = wid + (int64_t)nw * (32 * g + lane);
+          uint32_t todo = __ballot_sync(0xffffffffu, r < nrun && s_pre[r + 1] > s_pre[r]);
+          while (todo != 0u) {
+            const int ka = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            int kb = -1;
+            if (todo != 0u) {
+              kb = __ffs(todo) - 1;
+              todo &= todo - 1u;
+            }
+            const int k = half ? kb : ka;
+            const int64_t rr = wid + (int64_t)nw * (32 * g + (k < 0 ? 0 : k));
+            const int64_t w = rr * kRunWords + hl;
+            const uint32_t m = (k >= 0 && w < words) ? flag_mask16(aw[w]) : 0u;
+            const int c = __popc(m);
+            int ci = c;
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+              const int t = __shfl_up_sync(0xffffffffu, ci, o, 16);
+              if (hl >= o) ci += t;
+            }
+            int o = (k >= 0 ? s_pre[rr] : 0) + ci - c;
+            for (uint32_t mm = m; mm != 0u; mm &= mm - 1u, ++o)
+              if (o < kTailCap) s_list[o] = (int)(w * 16 + __ffs(mm) - 1);
+          }
+        }
+        __syncthreads();
+      }
     }
-  } else if (stepping) {
+  }
+  if (stepping && !listed) {
     for (int v0 = 0; v0 < kTailLanes; v0 += blockDim.x) {
       const int v = v0 + (int)threadIdx.x;
       const int64_t w0 = (int64_t)v * per;

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_tail(Dev<T> D) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  tail_block(D, mode);
+  tail_block<T, true>(D, mode);
 }
 
 // After pdn_set_impactor: the striker of the first step to be computed.
