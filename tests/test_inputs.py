@@ -69,3 +69,35 @@ def test_striker_gravity_and_integrator(coupon):
     # the contact surface is the top face
     p = coupon.plate
     assert np.all(p.X[2, p.surf] == H) and p.n_surf == 208 * 139
+
+
+def test_batch_of_64_plates_recipe():
+    """The batched workload: 64 seeded plates whose sizes are drawn
+    log-uniformly in 8k-400k hex8 and rounded to whole in-plane grids
+    (7,776 to 396,396 hex8, 6.23 M in all), 8-24 plies, strikers of 1-6 kg
+    at 1-5 m/s, one stable step for all (same spacing and ply thickness)."""
+    ws = pi.batch_plates()
+    assert len(ws) == 64
+    nh = np.array([w.plate.n_hex for w in ws])
+    assert nh.min() == 7776 and nh.max() == 396396 and nh.sum() == 6229848
+    assert all(8 <= len(w.plate.ply_angle_deg) <= 24 for w in ws)
+    assert all(1.0e-3 <= w.mass <= 6.0e-3 and 1000.0 <= w.speed <= 5000.0 for w in ws)
+    h = {round(w.plate.dims[0] / w.plate.grid[0], 12) for w in ws}
+    t = {round(w.plate.dims[2] / len(w.plate.ply_angle_deg), 12) for w in ws}
+    assert len(h) == 1 and len(t) == 1
+    assert len({w.name for w in ws}) == 64
+
+
+def test_large_plate_recipe():
+    """The 100x150x4.4 mm plate refined to 400x600x32 hex8 (two elements per
+    ply, 7.68 M hex), interfaces between plies of different angle, 5.5 kg at
+    4 m/s."""
+    w = pi.large_fp32_plate()
+    p = w.plate
+    assert p.dims == pytest.approx((100.0, 150.0, 4.4))
+    assert p.n_hex == 400 * 600 * 32
+    n_if = sum(1 for a, b in zip(p.ply_angle_deg[:-1], p.ply_angle_deg[1:]) if a != b)
+    assert len(p.ply_angle_deg) == 16 and p.n_coh == n_if * 400 * 600
+    assert p.n_nodes == 401 * 601 * (33 + n_if)
+    R, mass, centre, vel = w.impactor()
+    assert (R, mass, vel) == (8.0, 5.5e-3, (0.0, 0.0, -4000.0))
