@@ -516,6 +516,54 @@ def test_central_difference_stability_limit():
     assert growth[1.03] > 1e3
 
 
+@pytest.mark.parametrize("phi", [1.0, 1.033])
+def test_tw_phase_volume_contraction(phi):
+    """Tchamwa-Wielgosz with parameter phi (Sec. 2.2.1) on one free node of a
+    hex, linear regime: the map (d, dt v) -> (d', dt v') over a step has
+    determinant det(I - (phi - 1) dt^2 M^-1 K) (block determinant of
+    [[I - phi dt^2 B, I], [-dt^2 B, I]], B = M^-1 K): phase volume is kept at
+    phi = 1 (central difference) and shrinks by that factor per step for
+    phi > 1, the scheme's numerical damping.  The map is measured from six
+    independent small starts (1e-7 mm; smaller starts lose digits to
+    rounding over many steps), over one step and over 40."""
+    plate = pi.make_plate(1.0, 1.0, 1.0, 1, 1, [0.0], 1, cohesive=False, clamp="none")
+    plate.fixed[:] = 7
+    free = 6
+    plate.fixed[free] = 0
+    mat = pi.material_im7_like_config(t_ply=1.0, spread=0.0)
+    probe = oracle.Model(plate, mat)
+    h = 1e-7
+    K = np.zeros((3, 3))
+    for c in range(3):
+        d = np.zeros((3, plate.n_nodes))
+        d[c, free] = h
+        probe.set_state(d, np.zeros_like(d))
+        K[:, c] = probe.internal_force()[:, free] / h
+    m = probe.mass()[free]
+    dt = 0.5 * 2.0 / math.sqrt(np.linalg.eigvalsh(0.5 * (K + K.T)).max() / m)
+    per_step = np.linalg.det(np.eye(3) - (phi - 1.0) * dt * dt * K / m)
+    for n, rel in ((1, 1e-12), (40, 1e-6)):
+        A = np.zeros((6, 6))
+        for col in range(6):
+            d = np.zeros((3, plate.n_nodes))
+            v = np.zeros((3, plate.n_nodes))
+            if col < 3:
+                d[col, free] = h
+            else:
+                v[col - 3, free] = h / dt
+            M = oracle.Model(plate, mat, phi=phi, dt=dt)
+            M.set_state(d, v)
+            M.step(n)
+            dn, vn, _ = M.state()
+            A[:3, col] = dn[:, free] / h
+            A[3:, col] = dt * vn[:, free] / h
+        assert np.linalg.det(A) == pytest.approx(per_step ** n, rel=rel)
+    if phi == 1.0:
+        assert per_step == 1.0
+    else:
+        assert per_step ** 40 < 0.5  # 40 steps of numerical damping are visible
+
+
 def test_contact_set_equals_brute_force():
     """Tiny plate pushed into the sphere: after one (vanishingly short) step
     the contact set is exactly {j : |X_j + d_j - c| < R}."""
