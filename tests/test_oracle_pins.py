@@ -564,6 +564,31 @@ def test_tw_phase_volume_contraction(phi):
         assert per_step ** 40 < 0.5  # 40 steps of numerical damping are visible
 
 
+def test_free_plate_keeps_its_linear_momentum():
+    """A free plate (nothing held, no gravity, striker far away) with
+    interfaces, damage and plasticity on, started from a damaging seeded
+    state: every element's nodal forces sum to zero (the shape-function
+    derivatives sum to zero; interface tractions act in equal and opposite
+    pairs), so the lumped momentum sum_j m_j v_j stays at its initial value
+    to rounding while the plate deforms and damages."""
+    plate, mat, M = _tiny_model(nx=5, ny=4, plies=(0.0, 90.0, 45.0), clamp="none", cohesive=True,
+                                damage_on=True, plasticity_on=True)
+    Lx, Ly, _ = plate.dims
+    d0, v0 = pi.seeded_state(plate, 11, amp=0.03, vamp=400.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.08, 1.2))
+    v0 = v0 + np.array([[120.0], [-80.0], [35.0]])  # a rigid drift on top
+    M.set_state(d0, v0)
+    M.set_impactor(1.0, 1e-3, (0.5 * Lx, 0.5 * Ly, 1e4), (0.0, 0.0, -1.0))
+    m = M.mass()
+    p0 = (m * v0).sum(axis=1)
+    scale = (m * np.abs(v0)).sum(axis=1).max()
+    for _ in range(4):
+        assert M.step(50) == 0
+        _, v, _ = M.state()
+        assert np.abs((m * v).sum(axis=1) - p0).max() <= 1e-12 * scale
+    hist, rD = M.history()
+    assert (hist[:, :, :4] > 1.0).any() or (rD > 0).any(), "the state must damage"
+
+
 def test_contact_set_equals_brute_force():
     """Tiny plate pushed into the sphere: after one (vanishingly short) step
     the contact set is exactly {j : |X_j + d_j - c| < R}."""
