@@ -1,0 +1,52 @@
+"""Properties of the CUDA path that hold at any size, checked at the
+benchmark plate's full size (128x192x16 hex8 with its interfaces) through
+the C ABI.
+
+Linear momentum: every element's nodal forces sum to zero (the shape-function
+derivatives sum to zero; interface tractions act in equal and opposite
+pairs), so a free plate with no gravity and no contact keeps sum_j m_j v_j.
+FP64 element arithmetic keeps it to rounding; FP32 element forces leave a
+residual of FP32 rounding per element (about 1e-7 of the element force),
+which bounds the drift far below the momentum itself."""
+import numpy as np
+import pytest
+
+import pdn_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2301_05552_gb300 as p
+    p.lib()
+    return p
+
+
+@pytest.mark.parametrize("precision,rel", [("fp64", 1e-11), ("fp32", 1e-6)])
+def test_free_full_size_plate_keeps_its_linear_momentum(pkg, precision, rel):
+    w = pi.damage_fp32_plate()
+    p = pi.make_plate(*w.plate.dims, w.plate.grid[0], w.plate.grid[1], list(w.plate.ply_angle_deg), 1,
+                      cohesive=True, clamp="none")
+    Lx, Ly, H = p.dims
+    d0, v0 = pi.seeded_state(p, 3, amp=0.02, vamp=300.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.05, 4.0))
+    v0 = v0 + np.array([[150.0], [-90.0], [40.0]])
+    prec = pkg.PDN_FP64 if precision == "fp64" else pkg.PDN_FP32_FORCE
+    ctx = pkg.pdn_init_mesh(p, w.material, precision=prec)
+    # the striker far above the plate: no contact
+    pkg.pdn_set_impactor(ctx, 8.0, 5.5e-3, (0.5 * Lx, 0.5 * Ly, H + 1e4), (0.0, 0.0, -1.0))
+    pkg.pdn_set_state(ctx, d0, v0)
+    # lumped masses from the same mesh on the host: rho V / 8 per hex corner
+    X = p.X
+    lo, hi = X[:, p.hex[:, 0]], X[:, p.hex[:, 6]]
+    vol = np.prod(hi - lo, axis=0)
+    m = np.zeros(p.n_nodes)
+    np.add.at(m, p.hex.ravel(), np.repeat(w.material["rho"] * vol / 8.0, 8))
+    p0 = (m * v0).sum(axis=1)
+    scale = (m * np.abs(v0)).sum(axis=1).max()
+    for _ in range(4):
+        pkg.pdn_step(ctx, 25)
+        _, v, _ = pkg.pdn_get_state(ctx)
+        assert np.abs((m * v).sum(axis=1) - p0).max() <= rel * scale
+    assert pkg.pdn_get_info(ctx)["step"] == 100
+    ctx.close()
