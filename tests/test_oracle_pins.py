@@ -589,6 +589,26 @@ def test_free_plate_keeps_its_linear_momentum():
     assert (hist[:, :, :4] > 1.0).any() or (rD > 0).any(), "the state must damage"
 
 
+def test_oracle_is_independent_of_its_thread_count():
+    """The oracle's element loop runs on OpenMP threads (the timed CPU
+    baseline uses every core) while assembly stays in element order: a
+    damaging run with interfaces gives bitwise the same state and force
+    history on 1, 3 and 8 threads."""
+    w = pi.damage_fp32_plate(nx=16, ny=24, plies=8, Lx=12.5, Ly=18.75, H=2.2, steps=40)
+    Lx, Ly, H = w.plate.dims
+    st = pi.seeded_state(w.plate, 7, amp=0.02, vamp=300.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.12, 1.5))
+    runs = []
+    for nt in (1, 3, 8):
+        m = oracle.model_for(w, n_threads=nt)
+        m.set_state(*st)
+        assert m.step(40) == 0
+        d, v, _ = m.state()
+        runs.append((d.copy(), v.copy(), m.force_history().copy()))
+        m.close()
+    for r in runs[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
+
+
 def test_contact_set_equals_brute_force():
     """Tiny plate pushed into the sphere: after one (vanishingly short) step
     the contact set is exactly {j : |X_j + d_j - c| < R}."""
