@@ -185,6 +185,32 @@ def dist_setup():
     return ws, rank, local
 
 
+def divided_name(w) -> str:
+    """Name of the AS4 coupon divided once (the mesh-multiplication workload)."""
+    return w.name.replace("207x138x8", "414x276x16") + "_divided_on_device"
+
+
+def reference_workload(args):
+    """The workload the reference arm times for --workload: the oracle runs the
+    same plate as the GPU arm (for the divided coupon, divided by the oracle's
+    own mesh multiplication; for the learned law, the exact law it stands in
+    for), under the GPU arm's workload name."""
+    import dataclasses
+
+    import pdn_inputs as pi
+    if args.workload == "mmu":
+        import oracle.mesh_multiply as omm
+        w = pi.as4_frame_plate(steps=args.steps, seed=args.seed)
+        g = omm.multiply_plate(w.plate, 1)
+        nx, ny, nz = w.plate.grid
+        fine = pi.Plate(X=g["X"], hex=g["hex"], coh=g["coh"], ply_of_hex=g["ply_of_hex"],
+                        ply_of_coh=g["ply_of_coh"], ply_angle_deg=w.plate.ply_angle_deg, fixed=g["fixed"],
+                        surf=g["surf"], dims=w.plate.dims, grid=(2 * nx, 2 * ny, 2 * nz))
+        return dataclasses.replace(w, plate=fine), divided_name(w)
+    w = workload_for(args)
+    return w, (w.name + "_learned_law" if args.workload == "surrogate" else w.name)
+
+
 def workload_for(args):
     import pdn_inputs as pi
     if getattr(args, "workload", "plate") == "large":
@@ -218,14 +244,14 @@ def run_reference(args, ws, rank):
     budget = max(10.0, min(120.0, args.ref_seconds))
     if args.workload == "batch64":
         return run_reference_batch(args, cores, budget)
-    w = workload_for(args)
+    w, name = reference_workload(args)
     # warm-up steps are part of the bounded sample's set-up
     rate, n, dt = oracle_rate(w, budget, max(1, args.steps), cores)
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_hex": w.plate.n_hex, "n_coh": w.plate.n_coh,
+        "config": {"workload": name, "n_hex": w.plate.n_hex, "n_coh": w.plate.n_coh,
                    "n_nodes": w.plate.n_nodes, "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n} of the workload's explicit steps from rest, FP64 oracle, {cores} threads"},
@@ -508,7 +534,6 @@ def run_mmu(args, ws, rank, local):
     import numpy as np
     import torch
 
-    import oracle.mesh_multiply as omm
     import paper_2301_05552_gb300 as pkg
     import pdn_inputs as pi
 
@@ -589,7 +614,7 @@ def run_mmu(args, ws, rank, local):
         "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {
-            "workload": w.name.replace("207x138x8", "414x276x16") + "_divided_on_device",
+            "workload": divided_name(w),
             "n_hex": nh1, "n_coh": nc1, "n_nodes": nn1, "n_surf": ns1, "dt_s": info["dt"],
             "simulated_us": info["time"] * 1e6, "f_peak_N": float(fh.max()) if len(fh) else 0.0,
             "step_repeats": int(repeats), "l2": "inputs larger than L2 (working set %.0f MB)"
@@ -613,6 +638,7 @@ def run_mmu(args, ws, rank, local):
         "clocks": clocks.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        import oracle.mesh_multiply as omm
         # the oracle's division on a bounded sample: the cut-down coupon
         cut = pi.reduced_as4_frame_plate(nx=80, ny=56).plate
         t0 = time.perf_counter()
