@@ -589,6 +589,41 @@ def test_free_plate_keeps_its_linear_momentum():
     assert (hist[:, :, :4] > 1.0).any() or (rD > 0).any(), "the state must damage"
 
 
+def test_free_spinning_plate_keeps_its_angular_momentum():
+    """Central difference (TW with phi = 1, Sec. 2.2.1) on a free plate
+    without interfaces, spinning and deforming with damage and plasticity on:
+    with the stored state (d^k, v^k), d^k = d^(k-1) + dt v^k, the quantity
+    J = sum_j m_j (X_j + d_j) x v_j changes per step by dt times the total
+    torque of the internal forces at the previous positions, which is zero
+    when P = S F^T with S symmetric (sum_a x_a (x) grad N_a = F at every Gauss
+    point, so the torque is the skew part of F S F^T).  J is kept to
+    rounding; a transposed stress product or a mispaired position update
+    would not keep it."""
+    plate, mat, M = _tiny_model(nx=4, ny=5, plies=(30.0, 30.0, -60.0), clamp="none", cohesive=False,
+                                damage_on=True, plasticity_on=True)
+    Lx, Ly, H = plate.dims
+    d0, v0 = pi.seeded_state(plate, 5, amp=0.03, vamp=400.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.08, 1.2))
+    xc = plate.X.mean(axis=1, keepdims=True)
+    omega = np.array([[3.0e3], [-2.0e3], [4.0e3]])  # rad/s
+    v0 = v0 + np.cross(omega.T, (plate.X - xc).T).T
+    M.set_state(d0, v0)
+    M.set_impactor(1.0, 1e-3, (0.5 * Lx, 0.5 * Ly, 1e4), (0.0, 0.0, -1.0))
+    m = M.mass()
+
+    def J(d, v):
+        x = plate.X + d
+        return (m * np.cross(x.T, v.T).T).sum(axis=1)
+
+    j0 = J(d0, v0)
+    scale = (m * np.linalg.norm(plate.X + d0, axis=0) * np.linalg.norm(v0, axis=0)).sum()
+    for _ in range(4):
+        assert M.step(50) == 0
+        d, v, _ = M.state()
+        assert np.abs(J(d, v) - j0).max() <= 1e-12 * scale
+    hist, _ = M.history()
+    assert (hist[:, :, :4] > 1.0).any(), "the state must damage"
+
+
 def test_oracle_is_independent_of_its_thread_count():
     """The oracle's element loop runs on OpenMP threads (the timed CPU
     baseline uses every core) while assembly stays in element order: a
