@@ -7,7 +7,12 @@ derivatives sum to zero; interface tractions act in equal and opposite
 pairs), so a free plate with no gravity and no contact keeps sum_j m_j v_j.
 FP64 element arithmetic keeps it to rounding; FP32 element forces leave a
 residual of FP32 rounding per element (about 1e-7 of the element force),
-which bounds the drift far below the momentum itself."""
+which bounds the drift far below the momentum itself.
+
+Angular momentum: without interface elements (whose mixed-mode tractions are
+not parallel to the opening), central difference keeps
+sum_j m_j (X_j + d_j) x v_j of the stored state, because the internal forces
+of P = S F^T with S symmetric exert no torque at any Gauss point."""
 import numpy as np
 import pytest
 
@@ -49,4 +54,39 @@ def test_free_full_size_plate_keeps_its_linear_momentum(pkg, precision, rel):
         _, v, _ = pkg.pdn_get_state(ctx)
         assert np.abs((m * v).sum(axis=1) - p0).max() <= rel * scale
     assert pkg.pdn_get_info(ctx)["step"] == 100
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,rel", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_free_spinning_full_size_plate_keeps_its_angular_momentum(pkg, precision, rel):
+    """The benchmark plate's mesh and layup without interface elements (plies
+    bonded), free, spinning and deforming: with the stored state (d, v) of
+    central difference, sum_j m_j (X_j + d_j) x v_j changes per step only by
+    the internal forces' torque, zero for P = S F^T with S symmetric at every
+    Gauss point; FP32 element arithmetic leaves rounding."""
+    w = pi.damage_fp32_plate()
+    p = pi.make_plate(*w.plate.dims, w.plate.grid[0], w.plate.grid[1], list(w.plate.ply_angle_deg), 1,
+                      cohesive=False, clamp="none")
+    Lx, Ly, H = p.dims
+    d0, v0 = pi.seeded_state(p, 5, amp=0.02, vamp=300.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.05, 4.0))
+    xc = p.X.mean(axis=1, keepdims=True)
+    omega = np.array([[40.0], [-30.0], [60.0]])  # rad/s: up to about 5 m/s at the corners
+    v0 = v0 + np.cross(omega.T, (p.X - xc).T).T
+    prec = pkg.PDN_FP64 if precision == "fp64" else pkg.PDN_FP32_FORCE
+    ctx = pkg.pdn_init_mesh(p, w.material, precision=prec)
+    pkg.pdn_set_impactor(ctx, 8.0, 5.5e-3, (0.5 * Lx, 0.5 * Ly, H + 1e4), (0.0, 0.0, -1.0))
+    pkg.pdn_set_state(ctx, d0, v0)
+    lo, hi = p.X[:, p.hex[:, 0]], p.X[:, p.hex[:, 6]]
+    m = np.zeros(p.n_nodes)
+    np.add.at(m, p.hex.ravel(), np.repeat(w.material["rho"] * np.prod(hi - lo, axis=0) / 8.0, 8))
+
+    def J(d, v):
+        return (m * np.cross((p.X + d).T, v.T).T).sum(axis=1)
+
+    j0 = J(d0, v0)
+    scale = (m * np.linalg.norm(p.X + d0, axis=0) * np.linalg.norm(v0, axis=0)).sum()
+    for _ in range(4):
+        pkg.pdn_step(ctx, 25)
+        d, v, _ = pkg.pdn_get_state(ctx)
+        assert np.abs(J(d, v) - j0).max() <= rel * scale
     ctx.close()
