@@ -99,3 +99,21 @@ def test_plate_generator_topology():
     assert sorted(ang[:8]) == [-45.0, -45.0, 0.0, 0.0, 45.0, 45.0, 90.0, 90.0]
     w1 = pi.plain_fp64_plate()
     assert (w1.plate.n_hex, w1.plate.n_nodes, w1.plate.n_surf) == (8192, 9801, 1089)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_headers_compile_as_plain_c_and_cpp(lang, std):
+    """Each public header stands alone as C99 and as C++17 with strict
+    warnings: the boundary is plain C types, pointers and sizes."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = f'#include "{h}"\n'
+        r = subprocess.run([cc, std, "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-x", lang,
+                            "-I", os.path.join(ROOT, "include"), "-"], input=src, capture_output=True, text=True)
+        assert r.returncode == 0, (h, r.stderr)
