@@ -670,6 +670,38 @@ def test_contact_set_equals_brute_force():
     assert np.all(lam[act.astype(bool)] >= 0.0)
 
 
+def test_contact_nodes_lie_on_the_sphere_and_move_with_it():
+    """Dirichlet condition of the PDN step (Sec. 2.1, Algorithm 1, rigid body
+    first): after every committed step each node of the contact set lies on
+    the striker's sphere at its current centre and its velocity along the
+    sphere normal is the striker's (projection along n; a projection onto the
+    previous step's sphere or with the gap's sign flipped fails by orders of
+    magnitude)."""
+    plate = pi.make_plate(8.0, 8.0, 1.0, 32, 32, [0.0, 90.0], 1, cohesive=False)
+    mat = pi.material_im7_like_config(t_ply=0.5, spread=0.0)
+    M = oracle.Model(plate, mat)
+    R = 4.0
+    M.set_impactor(R, 1e-3, (4.0, 4.0, 1.0 + R + 1e-4), (0.0, 0.0, -5000.0))
+    most = 0
+    for _ in range(30):
+        assert M.step(50) == 0
+        act, _ = M.active()
+        on = act.astype(bool)
+        if not on.any():
+            continue
+        most = max(most, int(on.sum()))
+        d, v, _ = M.state()
+        imp = M.impactor()
+        c, w = np.asarray(imp["centre"]), np.asarray(imp["velocity"])
+        s = plate.surf[on]
+        x = plate.X[:, s] + d[:, s]
+        r = np.linalg.norm(x - c[:, None], axis=0)
+        n = (x - c[:, None]) / r
+        assert np.abs(r - R).max() <= 1e-13 * R
+        assert np.abs(((v[:, s] - w[:, None]) * n).sum(axis=0)).max() <= 1e-13 * np.abs(w).max()
+    assert most >= 10
+
+
 def test_reactions_never_adhesive_and_release_happens():
     """Through loading and rebound every committed contact node carries a
     compressive reaction (Eq. anodes); at separation the adhesive node is
