@@ -90,3 +90,36 @@ def test_free_spinning_full_size_plate_keeps_its_angular_momentum(pkg, precision
         d, v, _ = pkg.pdn_get_state(ctx)
         assert np.abs(J(d, v) - j0).max() <= rel * scale
     ctx.close()
+
+
+def test_contact_nodes_of_the_full_size_plate_lie_on_the_sphere(pkg):
+    """The benchmark plate (FP32 elements, FP64 nodal state and contact):
+    after committed steps each node of the contact set lies on the striker's
+    sphere at its current centre and moves with the striker along the sphere
+    normal (Dirichlet condition, Sec. 2.1; projection and state in FP64).
+    The first 1,800 steps cover the start of contact (the set holds the node
+    under the striker at the sampled steps); the many-node case is pinned on
+    the oracle."""
+    w = pi.damage_fp32_plate()
+    p = w.plate
+    ctx = pkg.pdn_init_mesh(p, w.material, precision=pkg.PDN_FP32_FORCE)
+    R, mass, centre, vel = w.impactor()
+    pkg.pdn_set_impactor(ctx, R, mass, centre, vel)
+    most = 0
+    for _ in range(6):
+        pkg.pdn_step(ctx, 300)
+        act, _ = pkg.pdn_get_contact(ctx)
+        on = act.astype(bool)
+        if not on.any():
+            continue
+        most = max(most, int(on.sum()))
+        d, v, imp = pkg.pdn_get_state(ctx)
+        c, wv = np.asarray(imp["centre"]), np.asarray(imp["velocity"])
+        s = p.surf[on]
+        x = p.X[:, s] + d[:, s]
+        r = np.linalg.norm(x - c[:, None], axis=0)
+        n = (x - c[:, None]) / r
+        assert np.abs(r - R).max() <= 1e-12 * R
+        assert np.abs(((v[:, s] - wv[:, None]) * n).sum(axis=0)).max() <= 1e-12 * np.abs(wv).max()
+    assert most >= 1
+    ctx.close()
