@@ -243,6 +243,24 @@ int pdn_set_state(pdn_ctx *ctx, const double *d, const double *v);
  * (0 where inactive).  Either pointer may be NULL. */
 int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda);
 
+/* Committed damage history, for checkpoints and for checks against another
+ * solver of the same model.  hist [7][8][n_hex]: field f of Gauss point g of
+ * hex e at (f*8 + g)*n_hex + e, fields rFT rFC rMT rMC gp12 gp13 pbar
+ * (Algorithm 4: the four damage thresholds, the two plastic shear strains and
+ * the equivalent plastic strain).  rD [4][n_coh]: threshold of Newton-Cotes
+ * point p of interface element e at p*n_coh + e (Algorithm 5).  Both in the
+ * element precision: float for PDN_FP32_FORCE, double for PDN_FP64.  Host
+ * pointers owned by the caller; either may be NULL. */
+int pdn_get_history(pdn_ctx *ctx, void *hist, void *rD);
+
+/* Acceleration a^n of the committed step n ([3][n_nodes]): the lumped-mass
+ * acceleration with the contact reactions of that step (Sec. 2.2.1, Eq.
+ * anodes), 0 on constrained degrees of freedom -- the acceleration the next
+ * step's Tchamwa-Wielgosz predictor uses.  The library keeps the predicted
+ * velocity v' = v + dt a instead of a; the value returned is (v' - v)/dt,
+ * equal to a up to FP64 rounding.  Host pointer owned by the caller. */
+int pdn_get_acceleration(pdn_ctx *ctx, double *a);
+
 /* Nodal internal force f^i ([3][n_nodes]) at the committed state, computed
  * by the same element and gather kernels as a step, without advancing and
  * without changing the history. */
@@ -275,7 +293,7 @@ void pdn_destroy(pdn_ctx *ctx);
  * create a context (pdn_init_mesh allocates).  This call computes the same
  * quantity as pdn_internal_force, with the same element and gather kernels,
  * from caller buffers, and calls no allocating routine: its working memory
- * (element forces, mirrors, trial history, partial sums, control block,
+ * (element forces, slot positions, mirrors, trial history, control block,
  * about 10.8 MB) is a fixed array in device global memory that every device
  * loading this library holds until the process exits.
  *
@@ -286,7 +304,8 @@ void pdn_destroy(pdn_ctx *ctx);
  * gp12 gp13 pbar per Gauss point), read only, or NULL for the undamaged
  * state; csr_row [n_nodes+1] and csr_col [8 n_hex], the node -> element slot
  * map: csr_col[csr_row[j] .. csr_row[j+1]) lists 8*e + k for every hex e
- * whose local node k is j, in ascending order; f_int [3][n_nodes] output.
+ * whose local node k is j, in ascending order, so that csr_col is a
+ * permutation of 0 .. 8 n_hex - 1; f_int [3][n_nodes] output.
  * Host pointers: mat, ply_angle_deg [n_plies].  stream is a cudaStream_t
  * (NULL = legacy default stream); the call only enqueues work on it.
  *
@@ -295,11 +314,14 @@ void pdn_destroy(pdn_ctx *ctx);
  * NULL or a parameter is invalid; PDN_E_CUDA on a launch failure.  Device
  * contents are not validated (out-of-range ids are the caller's fault).
  *
- * The first call on a device looks up the device address of the scratch
- * array (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array: calls
- * whose work overlaps on the GPU (several streams or host threads on one
- * device) race and must be serialised by the caller. */
+ * Every call looks up the device address of the scratch array in the
+ * current context (cudaGetSymbolAddress, a host-side query), so a reset
+ * device or another context on the same device gets its own array.  The
+ * first call in a context loads the library's device code there; make it
+ * before any stream capture.  All calls share the one array and it keeps the
+ * last call's contents; each call rewrites what it reads.  Calls whose work
+ * overlaps on the GPU (several streams or host threads on one device) race
+ * and must be serialised by the caller. */
 int pdn_internal_force_noalloc(int64_t n_nodes, int64_t n_hex, const int32_t *hex, const int8_t *ply_of_hex,
                                const double *X, const double *d, const void *history, const int32_t *csr_row,
                                const int32_t *csr_col, const pdn_material *mat, const double *ply_angle_deg,

@@ -80,6 +80,7 @@ def lib():
             L.orc_step.restype = C.c_int
             L.orc_get_state.argtypes = [C.c_void_p, dp, dp, dp]
             L.orc_set_state.argtypes = [C.c_void_p, dp, dp]
+            L.orc_install_state.argtypes = [C.c_void_p, dp, dp, dp, C.POINTER(C.c_uint8), dp, C.c_int64]
             L.orc_get_impactor.argtypes = [C.c_void_p, dp]
             L.orc_get_info.argtypes = [C.c_void_p, dp]
             L.orc_get_mass.argtypes = [C.c_void_p, dp]
@@ -264,6 +265,19 @@ class Model:
         d = np.ascontiguousarray(d, dtype=np.float64)
         v = np.ascontiguousarray(v, dtype=np.float64)
         lib().orc_set_state(self.h, _p(d, C.c_double), _p(v, C.c_double))
+
+    def install_state(self, d, v, a, active, imp, step: int):
+        """Continue from another solver's committed state of step ``step``:
+        d, v, a [3, nn]; active [ns] contact set; imp = dict(centre,
+        velocity, force, time) of the striker.  Nothing is recomputed."""
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        act = np.ascontiguousarray(active, dtype=np.uint8)
+        im = np.concatenate([np.asarray(imp["centre"], dtype=np.float64), np.asarray(imp["velocity"], dtype=np.float64),
+                             np.asarray(imp["force"], dtype=np.float64), [float(imp["time"])]])
+        lib().orc_install_state(self.h, _p(d, C.c_double), _p(v, C.c_double), _p(a, C.c_double),
+                                _p(act, C.c_uint8), _p(im, C.c_double), int(step))
 
     def impactor(self):
         out = np.zeros(10)

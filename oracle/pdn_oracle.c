@@ -1077,6 +1077,41 @@ void orc_set_state(orc_model *M, const double *d, const double *v) {
   acceleration_of_state(M);
 }
 
+/* Install a complete committed state of step `step` taken from another solver
+ * of the same model, so that the oracle continues from it: displacement,
+ * velocity and acceleration (SoA [3][nn]; the acceleration the next
+ * predictor uses), the contact set active[ns], and imp[10] = striker centre
+ * c[3], velocity w[3], the contact force F[3] of that step (held over the
+ * next step, Algorithm 1) and the time.  Nothing is recomputed.  The force
+ * history restarts empty; the history of the integration points is installed
+ * separately (orc_set_history). */
+void orc_install_state(orc_model *M, const double *d, const double *v, const double *a,
+                       const uint8_t *active, const double imp[10], int64_t step) {
+  for (int64_t j = 0; j < M->nn; ++j)
+    for (int i = 0; i < 3; ++i) {
+      int held = (M->fixed[j] >> i) & 1;
+      M->d[j * 3 + i] = held ? 0.0 : d[i * M->nn + j];
+      M->v[j * 3 + i] = held ? 0.0 : v[i * M->nn + j];
+      M->a[j * 3 + i] = held ? 0.0 : a[i * M->nn + j];
+    }
+  M->n_active = 0;
+  for (int64_t s = 0; s < M->ns; ++s) {
+    M->active[s] = active[s] ? 1 : 0;
+    M->lambda[s] = 0.0;
+    M->n_active += M->active[s];
+  }
+  for (int i = 0; i < 3; ++i) {
+    M->c[i] = imp[i];
+    M->w[i] = imp[3 + i];
+    M->F[i] = imp[6 + i];
+  }
+  M->time = imp[9];
+  M->step = step;
+  M->fhist_n = 0;
+  M->fpeak = 0.0;
+  M->status = ORC_OK;
+}
+
 void orc_get_impactor(const orc_model *M, double out[10]) {
   for (int i = 0; i < 3; ++i) {
     out[i] = M->c[i];

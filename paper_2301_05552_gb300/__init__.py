@@ -24,8 +24,8 @@ from . import _build
 __all__ = [
     "PdnError", "lib", "build",
     "pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
-    "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
-    "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
+    "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration",
+    "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
     "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
     "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
     "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
@@ -43,8 +43,8 @@ KERNELS = ["contact", "hex", "coh", "gather", "tail"]
 ERRORS = {-1: "PDN_E_ARG", -2: "PDN_E_CUDA", -3: "PDN_E_OOM", -4: "PDN_E_NONFINITE",
           -5: "PDN_E_RELEASE_LIMIT", -6: "PDN_E_TIMEOUT", -7: "PDN_E_UNSTABLE", -8: "PDN_E_STATE"}
 EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
-           "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_internal_force", "pdn_get_info",
-           "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
+           "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration",
+           "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
            "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
            "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
            "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
@@ -138,6 +138,8 @@ def lib():
             L.pdn_get_state.argtypes = [vp, dp, dp, dp]
             L.pdn_set_state.argtypes = [vp, dp, dp]
             L.pdn_get_contact.argtypes = [vp, C.POINTER(C.c_uint8), dp]
+            L.pdn_get_history.argtypes = [vp, vp, vp]
+            L.pdn_get_acceleration.argtypes = [vp, dp]
             L.pdn_internal_force.argtypes = [vp, dp]
             L.pdn_get_info.argtypes = [vp, C.POINTER(Info)]
             L.pdn_profile_kernels.argtypes = [vp, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_int64)]
@@ -194,8 +196,8 @@ def lib():
             for name in ("pdn_mesh_multiply", "pdn_refined_get_info", "pdn_refined_get", "pdn_init_refined"):
                 getattr(L, name).restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
-                         "pdn_get_contact", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels",
-                         "pdn_init_mesh"):
+                         "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration", "pdn_internal_force",
+                         "pdn_get_info", "pdn_profile_kernels", "pdn_init_mesh"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -368,6 +370,23 @@ def pdn_get_contact(ctx: Context):
     lam = np.zeros(max(ctx.n_surf, 1))
     _check(ctx, lib().pdn_get_contact(ctx.handle, _ptr(act, C.c_uint8), _ptr(lam, C.c_double)))
     return act[: ctx.n_surf], lam[: ctx.n_surf]
+
+
+def pdn_get_history(ctx: Context):
+    """Committed history: (hist [7, 8, n_hex], rD [4, n_coh]) in the element
+    precision (float32 for PDN_FP32_FORCE, float64 for PDN_FP64)."""
+    dt = np.float64 if pdn_get_info(ctx)["precision"] == PDN_FP64 else np.float32
+    h = np.zeros((7, 8, max(ctx.n_hex, 1)), dtype=dt)
+    r = np.zeros((4, max(ctx.n_coh, 1)), dtype=dt)
+    _check(ctx, lib().pdn_get_history(ctx.handle, h.ctypes.data_as(C.c_void_p), r.ctypes.data_as(C.c_void_p)))
+    return h[:, :, : ctx.n_hex], r[:, : ctx.n_coh]
+
+
+def pdn_get_acceleration(ctx: Context):
+    """Acceleration of the committed step, [3, n_nodes] float64."""
+    a = np.zeros((3, ctx.n_nodes))
+    _check(ctx, lib().pdn_get_acceleration(ctx.handle, _ptr(a, C.c_double)))
+    return a
 
 
 def pdn_internal_force(ctx: Context):

@@ -6,6 +6,7 @@
 // device-side state machine decides advance / repeat / halt, so the host only
 // checks the committed step count once per call.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -62,6 +63,16 @@ inline int grid_of(int64_t n, int b) {
   int64_t g = (n + b - 1) / b;
   return (int)(g < 1 ? 1 : g);
 }
+
+// NVTX range over a public call (named as the call), so that a profiler can
+// select the kernels one call launched (ncu --nvtx --nvtx-include "name/").
+// Header-only NVTX: without a profiler attached the push and pop are no-ops.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace
 
@@ -261,6 +272,37 @@ void hex_gauss(const double X[8][3], double detJ[8], double N[8][8]) {
     detJ[g] = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
   }
+}
+
+}  // namespace
+
+namespace {
+
+// The history of an element (interface element) flagged pristine is not
+// maintained in the buffers; it is the initial history (r = 1, plastic
+// strain 0; interface r_D = 0), which is what is returned for it.
+template <typename T>
+static int get_history_t(pdn_ctx *ctx, const Dev<T> &D, T *hist, T *rD) {
+  const int hb = ctx->ctl_host->hpar;
+  const int64_t nh = ctx->nh, nc = ctx->nc;
+  if (hist && nh > 0) {
+    std::vector<uint8_t> pf(nh);
+    PDN_CU(cudaMemcpy(hist, D.hist[hb], sizeof(T) * 7 * 8 * nh, cudaMemcpyDeviceToHost), "read history");
+    PDN_CU(cudaMemcpy(pf.data(), D.pflag[hb], nh, cudaMemcpyDeviceToHost), "read history flags");
+    for (int64_t e = 0; e < nh; ++e)
+      if (pf[e])
+        for (int f = 0; f < 7; ++f)
+          for (int g = 0; g < 8; ++g) hist[((int64_t)f * 8 + g) * nh + e] = f < 4 ? T(1) : T(0);
+  }
+  if (rD && nc > 0) {
+    std::vector<uint8_t> cf(nc);
+    PDN_CU(cudaMemcpy(rD, D.rD[hb], sizeof(T) * 4 * nc, cudaMemcpyDeviceToHost), "read interface history");
+    PDN_CU(cudaMemcpy(cf.data(), D.cflag[hb], nc, cudaMemcpyDeviceToHost), "read interface flags");
+    for (int64_t e = 0; e < nc; ++e)
+      if (cf[e])
+        for (int p = 0; p < 4; ++p) rD[(int64_t)p * nc + e] = T(0);
+  }
+  return PDN_OK;
 }
 
 }  // namespace
@@ -895,6 +937,7 @@ int autotune(pdn_ctx *ctx) {
 
 int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
   if (!ctx) return PDN_E_ARG;
+  NvtxRange range("pdn_step");
   if (nsteps < 0) return fail(ctx, PDN_E_ARG, "nsteps < 0");
   if (!ctx->has_imp) return fail(ctx, PDN_E_STATE, "pdn_set_impactor must be called before pdn_step");
   int rc = read_ctl(ctx);
@@ -925,6 +968,7 @@ int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
 
 int pdn_profile_kernels(pdn_ctx *ctx, int64_t nsteps, float *ms_per_launch, int64_t *launches) {
   if (!ctx) return PDN_E_ARG;
+  NvtxRange range("pdn_profile_kernels");
   if (nsteps < 0) return fail(ctx, PDN_E_ARG, "nsteps < 0");
   if (!ctx->has_imp) return fail(ctx, PDN_E_STATE, "pdn_set_impactor must be called first");
   if (ctx->prof_ev.empty()) {
@@ -1095,8 +1139,57 @@ int pdn_get_contact(pdn_ctx *ctx, uint8_t *active, double *lambda) {
   }
 }
 
+static int pdn_get_history_body(pdn_ctx *ctx, void *hist, void *rD) {
+  if (!ctx) return PDN_E_ARG;
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  if (ctx->precision == PDN_FP64)
+    return get_history_t<double>(ctx, ctx->Dd, static_cast<double *>(hist), static_cast<double *>(rD));
+  return get_history_t<float>(ctx, ctx->Df, static_cast<float *>(hist), static_cast<float *>(rD));
+}
+
+int pdn_get_history(pdn_ctx *ctx, void *hist, void *rD) {
+  try {
+    return pdn_get_history_body(ctx, hist, rD);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
+}
+
+// The committed state sits in the node buffer dpar ^ 1 and the prediction of
+// the next step (v' = v + dt a, before contact) in buffer dpar; no pass has
+// touched the prediction since the commit.
+static int pdn_get_acceleration_body(pdn_ctx *ctx, double *a) {
+  if (!ctx) return PDN_E_ARG;
+  if (!a) return fail(ctx, PDN_E_ARG, "a is NULL");
+  int rc = read_ctl(ctx);
+  if (rc) return rc;
+  const int b = ctx->ctl_host->dpar;
+  const int64_t n3 = 3 * ctx->nn;
+  double *const *vv = ctx->precision == PDN_FP64 ? ctx->Dd.v : ctx->Df.v;
+  std::vector<double> vp(n3);
+  PDN_CU(cudaMemcpy(vp.data(), vv[b], sizeof(double) * n3, cudaMemcpyDeviceToHost), "read predicted v");
+  PDN_CU(cudaMemcpy(a, vv[b ^ 1], sizeof(double) * n3, cudaMemcpyDeviceToHost), "read v");
+  const double idt = 1.0 / ctx->dt;
+  for (int64_t k = 0; k < n3; ++k) a[k] = (vp[k] - a[k]) * idt;
+  return PDN_OK;
+}
+
+int pdn_get_acceleration(pdn_ctx *ctx, double *a) {
+  try {
+    return pdn_get_acceleration_body(ctx, a);
+  } catch (const std::bad_alloc &) {
+    return PDN_E_OOM;
+  } catch (...) {
+    return PDN_E_ARG;
+  }
+}
+
 int pdn_internal_force(pdn_ctx *ctx, double *f_int) {
   if (!ctx) return PDN_E_ARG;
+  NvtxRange range("pdn_internal_force");
   if (!f_int) return fail(ctx, PDN_E_ARG, "f_int is NULL");
   int rc = read_ctl(ctx);
   if (rc) return rc;

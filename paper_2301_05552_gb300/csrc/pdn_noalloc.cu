@@ -12,17 +12,19 @@
 // array of fixed size, so it allocates nothing.
 //
 // The scratch array lives on every device that loads this library until the
-// process exits.  All calls share it and it keeps the last call's contents:
-// each call rewrites every scratch byte it reads before reading it (control
-// block, mirrors, history when none is given), so nothing depends on what an
-// earlier call left.  Calls whose work overlaps on the GPU (different streams
-// or host threads on the same device) race on the array.
+// process exits.  All calls share it and it keeps the last call's contents.
+// Given inputs that meet the preconditions stated in pdn.h (in particular a
+// csr_col that is a permutation of the element slots, as every node -> slot
+// map is), each call rewrites every scratch byte it reads before reading it
+// (control block, mirrors, slot positions, element forces, history when none
+// is given), so nothing depends on what an earlier call left.  Calls whose
+// work overlaps on the GPU (different streams or host threads on the same
+// device) race on the array.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "pdn.h"
@@ -33,7 +35,6 @@ using namespace pdn;
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kMaxDevices = 64;
 
 // Byte sizes of the scratch regions at the maxima, FP64 element precision
 // (the larger of the two).
@@ -52,11 +53,6 @@ constexpr size_t kOffPos = kOffFe + round256(kFeBytes);
 constexpr size_t kScratchBytes = kOffPos + round256(kPosBytes);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-// Device address of g_noalloc_scratch per device (host code may not use the
-// symbol itself as a device address).
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
 
 template <typename T>
 __global__ void k_noalloc_prepare(Ctl *ctl, const double *X, const double *d, typename Vec4T<T>::type *X4,
@@ -167,23 +163,17 @@ extern "C" int pdn_internal_force_noalloc(int64_t n_nodes, int64_t n_hex, const 
     return bad(PDN_E_ARG, "pdn_internal_force_noalloc: a required pointer is NULL");
   if (n_plies < 1 || n_plies > kMaxPlies) return bad(PDN_E_ARG, "n_plies must be in 1..64");
   if (precision != PDN_FP64 && precision != PDN_FP32_FORCE) return bad(PDN_E_ARG, "unknown precision");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return bad(PDN_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return bad(PDN_E_ARG, "device ordinal beyond the supported range");
+  // Device address of the scratch array in the context current on this
+  // thread.  Host code may not use the symbol itself as a device address.  It
+  // is looked up on every call (a host-side query that allocates nothing):
+  // after cudaDeviceReset, or under another context on the same device, the
+  // module is loaded again and the array can sit at another address, so a
+  // cached address could be stale.  The first call in a context loads the
+  // module there; make it before any stream capture.
   void *addr = nullptr;
-  {
-    // set-up once per device, with that device current (first call per device)
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-      e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        g_scratch_addr[dev] = nullptr;
-        return bad(PDN_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-      }
-    }
-    addr = g_scratch_addr[dev];
-  }
+  cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+  if (e != cudaSuccess || addr == nullptr)
+    return bad(PDN_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
   std::string why;
   cudaStream_t s = (cudaStream_t)stream;
   if (precision == PDN_FP64) {

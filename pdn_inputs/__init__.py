@@ -268,6 +268,9 @@ class Workload:
     steps: int
     phi: float = 1.0
     gravity: tuple = (0.0, 0.0, 0.0)
+    # steps of the impact advanced before a measured window opens, so that
+    # the window lies inside the contact phase (0: the window starts at rest)
+    preroll: int = 0
 
     def impactor(self):
         Lx, Ly, H = self.plate.dims
@@ -290,7 +293,7 @@ def damage_fp32_plate(nx: int = 128, ny: int = 192, plies: int = 16, elems_per_p
                       Lx: float = 100.0, Ly: float = 150.0, H: float = 4.4,
                       mass: float = 5.5e-3, speed: float = 3000.0, seed: int = 0,
                       steps: int = 20000, fp64: bool = False,
-                      strengths=(2300.0, 60.0, 90.0)) -> Workload:
+                      strengths=(2300.0, 60.0, 90.0), preroll: int = 1000) -> Workload:
     """100x150x4.4 mm plate, seeded quasi-isotropic 16-ply layup, intralaminar
     damage with seeded +/-5% strengths, interfaces between plies of different
     angle (GIc=0.3, GIIc=1.0 N/mm), rigid sphere R=8 mm, 5.5 kg at 3 m/s."""
@@ -298,14 +301,15 @@ def damage_fp32_plate(nx: int = 128, ny: int = 192, plies: int = 16, elems_per_p
     plate = make_plate(Lx, Ly, H, nx, ny, lay, elems_per_ply, cohesive=True)
     mat = material_im7_like_config(t_ply=H / plies, strengths=strengths, seed=seed)
     name = f"plate{Lx:g}x{Ly:g}x{H:g}_{nx}x{ny}x{plies * elems_per_ply}_{'fp64' if fp64 else 'fp32'}_damage"
-    return Workload(name, plate, mat, fp64, True, True, 8.0, mass, speed, 0.01, 0.5, steps)
+    return Workload(name, plate, mat, fp64, True, True, 8.0, mass, speed, 0.01, 0.5, steps,
+                    preroll=preroll)
 
 
 def large_fp32_plate(steps: int = 5000) -> Workload:
     """The same plate refined to 400x600x32 hex8 (two elements per ply),
     5.5 kg striker at 4 m/s."""
     return damage_fp32_plate(nx=400, ny=600, plies=16, elems_per_ply=2, speed=4000.0,
-                             steps=steps)
+                             steps=steps, preroll=1500)
 
 
 def as4_frame_plate(nx: int = 207, ny: int = 138, Lx: float = 150.0, Ly: float = 100.0,

@@ -644,6 +644,33 @@ def test_oracle_is_independent_of_its_thread_count():
         assert all(np.array_equal(a, b) for a, b in zip(runs[0], r))
 
 
+def test_installed_state_continues_bitwise():
+    """A committed state copied out of one oracle run (displacement, velocity,
+    acceleration, Gauss-point and interface history, contact set, striker)
+    and installed in a fresh model continues bit for bit as the run it came
+    from: the installed state is the whole state a step depends on (this is
+    how a GPU state is handed to the oracle)."""
+    w = pi.damage_fp32_plate(nx=16, ny=24, plies=8, Lx=12.5, Ly=18.75, H=2.2, mass=5.5e-3 / 64, speed=20000.0,
+                             steps=600)
+    a = oracle.model_for(w)
+    assert a.step(560) == 0
+    act, _ = a.active()
+    assert act.sum() > 0, "the snapshot must be in contact"
+    d, v, acc = a.state()
+    hist, rD = a.history()
+    assert (hist[:, :, :4] > 1.0).any(), "the snapshot must hold damage"
+    b = oracle.model_for(w)
+    b.set_history(hist, rD)
+    b.install_state(d, v, acc, act, a.impactor(), a.info()["step"])
+    assert a.step(40) == 0 and b.step(40) == 0
+    assert np.array_equal(a.force_history()[-40:], b.force_history())
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a.active()[0], b.active()[0])
+    assert a.impactor()["centre"][2] == b.impactor()["centre"][2]
+    assert b.info()["step"] == a.info()["step"] == 600
+
+
 def test_contact_set_equals_brute_force():
     """Tiny plate pushed into the sphere: after one (vanishingly short) step
     the contact set is exactly {j : |X_j + d_j - c| < R}."""
