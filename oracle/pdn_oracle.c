@@ -33,9 +33,14 @@
  * Parity status: the hex8 kinematics, the elastic law, the exponential
  * softening laws, the cohesive law, the time integrators and the contact
  * detection are pinned by closed forms and invariants in tests/.  The
- * multiaxial branches of the matrix failure criteria (combined tension/shear
- * and compression/shear with the fracture-angle terms) are checked only
- * at their uniaxial limits and continuity: parity unpinned beyond those.
+ * multiaxial branches of the intralaminar law are pinned against closed-form
+ * onset loci solved for the load factor with the ply's Poisson coupling:
+ * matrix tension with g = G_YT/G_SL < 1 under combined transverse tension
+ * and shear, matrix compression with the fracture-plane friction terms, the
+ * damaged compliance with Poisson terms (at D = 1 and in between) and the
+ * threshold coupling under mixed loading.  What stays unpinned is the
+ * choice of criteria itself (the readings of Algorithm 4 listed below),
+ * which the paper does not print.
  */
 #include <math.h>
 #include <stdint.h>

@@ -259,6 +259,207 @@ def test_transverse_shear_onset_and_branch_continuity():
         assert rs[0] == pytest.approx(rs[1], rel=1e-6)
 
 
+# Multiaxial branches of Algorithm 4, with the Poisson coupling of the real
+# ply (nu12 = nu13 = 0.3, nu23 = 0.45).  A proportional path in effective
+# stress is imposed through the textbook compliance (eps = H sigma~), and
+# the onset is located by bisection on the load factor, on the first point
+# where the oracle raises a damage threshold; it is compared with closed-form
+# onset loci of the published criteria, solved here for the load factor.
+
+def _poisson_material(**over):
+    m = pi.material_im7_like_config(t_ply=0.275, spread=0.0)
+    m.update(over)
+    return m
+
+
+def _onset_factor(mat, sig_dir, field, lo=0.0, hi=4.0, lc=0.3):
+    """Smallest load factor lam at which eps = lam H sig_dir raises history
+    field `field` (0 rFT, 1 rFC, 2 rMT, 3 rMC) above 1 from a pristine point."""
+    H = _compliance(mat)
+    base = H @ np.asarray(sig_dir, dtype=np.float64)
+
+    def moved(lam):
+        _, h = oracle.cdm_point(mat, lc, lam * base, damage_on=True, plasticity_on=False)
+        return h[field] > 1.0
+
+    assert not moved(lo) and moved(hi)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if moved(mid):
+            hi = mid
+        else:
+            lo = mid
+        if hi - lo <= 1e-13 * hi:
+            break
+    return 0.5 * (lo + hi)
+
+
+def _fracture_plane(mat):
+    """Transverse shear strength and friction coefficients of the 53 deg
+    fracture plane (Sec. 2.3.1 table constants; Maimi 2007 / Puck's plane)."""
+    a0 = math.radians(mat["alpha0_deg"])
+    ST = mat["YC"] * math.cos(a0) * (math.sin(a0) + math.cos(a0) / math.tan(2 * a0))
+    etaL = -mat["SL"] * math.cos(2 * a0) / (mat["YC"] * math.cos(a0) ** 2)
+    return ST, etaL
+
+
+@pytest.mark.parametrize("s22,t12,t13,s23", [(1.0, 1.0, 0.0, 0.0), (1.0, 0.4, 0.7, 0.0), (0.3, 1.0, 0.0, 0.5),
+                                             (1.0, 0.0, 0.0, 0.8)])
+def test_matrix_tension_onset_locus_with_g_below_one(s22, t12, t13, s23):
+    """Matrix tension under combined sigma22 > 0 and shear, g = G_YT/G_SL =
+    0.3 (the linear term of the criterion is active): the onset load factor
+    lam solves (1-g) lam a + g lam^2 a^2 + lam^2 (b^2 + c^2) = 1 with
+    a = s22/Y_T, b = tau_L/S_L, c = s23/S_T, i.e. the positive root of the
+    quadratic; with g = 1 the root would be 1/sqrt(a^2 + b^2 + c^2).  The
+    effective stress is the ply's full Poisson-coupled response."""
+    mat = _poisson_material()
+    g = mat["GYT"] / mat["GSL"]
+    assert g == pytest.approx(0.3)
+    ST, _ = _fracture_plane(mat)
+    sig = np.array([0.0, s22 * mat["YT"], 0.0, t12 * mat["SL"], t13 * mat["SL"], s23 * ST])
+    a = sig[1] / mat["YT"]
+    bb = (sig[3] ** 2 + sig[4] ** 2) / mat["SL"] ** 2
+    cc = (sig[5] / ST) ** 2
+    A2 = g * a * a + bb + cc
+    B1 = (1 - g) * a
+    lam = (-B1 + math.sqrt(B1 * B1 + 4 * A2)) / (2 * A2)
+    assert _onset_factor(mat, sig, 2) == pytest.approx(lam, rel=1e-9)
+    if a > 0 and (bb + cc) > 0:  # the linear term matters: the g = 1 locus is elsewhere
+        assert abs(lam - 1 / math.sqrt(a * a + bb + cc)) > 1e-3 * lam
+
+
+@pytest.mark.parametrize("q", [0.1, 0.35, 0.6, 0.85])
+def test_matrix_compression_onset_with_friction(q):
+    """Matrix compression sigma22 = -q Y_C with longitudinal shear tau_L: on
+    the 53 deg fracture plane the normal compression adds friction
+    eta_L |sigma22| to the longitudinal shear strength and uses up part of the
+    transverse one, so the onset shear is tau_L* = eta_L q Y_C + S_L
+    sqrt(1 - q^2) (eta_L > 0 for a0 > 45 deg; a sign slip in eta_L moves it by
+    2 eta_L q Y_C).  With transverse shear s23 instead, s23* = S_T
+    sqrt(1 - q^2)."""
+    mat = _poisson_material()
+    ST, etaL = _fracture_plane(mat)
+    assert etaL > 0
+    s22 = -q * mat["YC"]
+    tau_star = etaL * q * mat["YC"] + mat["SL"] * math.sqrt(1 - q * q)
+    # scale the whole stress state: onset at lam = 1 when tau_L = tau_star
+    sig = np.array([0.0, s22, 0.0, 0.6 * tau_star, 0.8 * tau_star, 0.0])
+    # along lam * sig both sigma22 and tau_L scale; solve the locus for lam
+    #   (lam q)^2 + ((lam tau* - eta_L lam q Y_C)/S_L)^2 = 1 -> lam = 1 exactly
+    assert _onset_factor(mat, sig, 3) == pytest.approx(1.0, rel=1e-9)
+    sig_t = np.array([0.0, s22, 0.0, 0.0, 0.0, ST * math.sqrt(1 - q * q)])
+    assert _onset_factor(mat, sig_t, 3) == pytest.approx(1.0, rel=1e-9)
+    # pure compression at the same ratio: onset at Y_C (lam = 1/q)
+    assert _onset_factor(mat, [0.0, s22, 0.0, 0.0, 0.0, 0.0], 3, hi=4.0 / q) == pytest.approx(1.0 / q, rel=1e-9)
+
+
+def _damaged_stress(mat, eps, D1, D2, D6):
+    """Nominal stress of the damaged ply (Maimi's damaged compliance): the
+    textbook compliance with H11 / (1 - D1), H22 / (1 - D2), H44, H55 /
+    (1 - D6), H66 / (1 - D2), the 33 term and the Poisson terms undamaged,
+    inverted with numpy.  At D = 1 the row and column of that direction drop
+    out (the direction carries no stress)."""
+    H = _compliance(mat)
+    keep = [i for i, D in ((0, D1), (1, D2), (2, 0.0), (3, D6), (4, D6), (5, D2)) if D < 1.0]
+    Hd = H.copy()
+    for i, D in ((0, D1), (1, D2), (3, D6), (4, D6), (5, D2)):
+        if D < 1.0:
+            Hd[i, i] = H[i, i] / (1.0 - D)
+    sig = np.zeros(6)
+    sub = np.ix_(keep, keep)
+    # the damaged directions are stress-free: their strains are free, so the
+    # others follow from the reduced compliance
+    sig[keep] = np.linalg.solve(Hd[sub], np.asarray(eps)[keep])
+    return sig
+
+
+def _crack_band_damage(r, lc, X, E, G):
+    A = 2 * lc * X * X / (2 * E * G - lc * X * X)
+    return 1.0 - math.exp(A * (1.0 - r)) / r
+
+
+def test_damaged_normal_block_with_poisson_coupling():
+    """Nominal stress of a damaged point with the real Poisson ratios, for
+    fixed thresholds (no growth along the strain): fibre damage D1 = 1
+    leaves sigma11 = 0 and the 22-33 block of the compliance; matrix damage
+    D2 = 1 leaves sigma22 = sigma23 = 0 and the 11-33 block; intermediate
+    damage follows the full damaged compliance (reduced diagonal, Poisson
+    terms kept).  The damage values follow the pinned crack-band law."""
+    mat = _poisson_material()
+    lc = 0.3
+    eps = np.array([2.0e-3, 1.5e-3, -1.0e-3, 2.0e-3, -1.5e-3, 1.0e-3])
+    big = 1.0e6  # exp(A (1 - r)) underflows: D = 1 exactly
+    # D1 = 1 (fibre tension threshold), matrix pristine
+    h = np.array([big, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0])
+    s, ho = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    assert np.array_equal(ho[:4], h[:4])
+    want = _damaged_stress(mat, eps, 1.0, 0.0, 0.0)
+    assert s[0] == 0.0
+    assert s == pytest.approx(want, rel=1e-12, abs=1e-12 * np.abs(want).max())
+    # D2 = D6 = 1 (matrix tension threshold), fibre pristine
+    h = np.array([1.0, 1.0, big, 1.0, 0.0, 0.0, 0.0])
+    s, _ = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    want = _damaged_stress(mat, eps, 0.0, 1.0, 1.0)
+    assert s[1] == 0.0 and s[5] == 0.0 and s[3] == 0.0
+    assert s == pytest.approx(want, rel=1e-12, abs=1e-12 * np.abs(want).max())
+    # intermediate damage: r_FT = 1.3, r_MT = 1.6
+    h = np.array([1.3, 1.0, 1.6, 1.0, 0.0, 0.0, 0.0])
+    s, ho = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    assert np.array_equal(ho[:4], h[:4]), "the strain must stay below the thresholds"
+    D1 = _crack_band_damage(1.3, lc, mat["XT"], mat["E1"], mat["GXT"])
+    D2 = _crack_band_damage(1.6, lc, mat["YT"], mat["E2"], mat["GYT"])
+    D6 = _crack_band_damage(1.6, lc, mat["SL"], mat["G12"], mat["GSL"])
+    want = _damaged_stress(mat, eps, D1, D2, D6)
+    assert s == pytest.approx(want, rel=1e-11)
+    # the Poisson coupling matters here: the uncoupled (diagonal) answer differs
+    diag = np.array([(1 - D1) * mat["E1"], (1 - D2) * mat["E2"], mat["E3"]]) * eps[:3]
+    assert abs(s[1] - diag[1]) > 0.1 * abs(s[1]) and abs(s[2] - diag[2]) > 0.1 * abs(diag[2])
+
+
+def test_threshold_coupling_and_shear_damage_under_mixed_loading():
+    """Compression damage carries over to tension in the same direction
+    (r_FT >= r_FC, r_MT >= r_MC) but not back; shear damage follows r_MT.
+    Fibre: sigma~11 = -1.1 X_C sets r_FC = r_FT = 1.1, so a later tensile
+    strain sees D1 = d_FT(1.1) > 0.  Matrix: sigma~22 = -1.25 Y_C sets
+    r_MC = r_MT = 1.25 (pure compression: phi_MC = |sigma22|/Y_C), so later
+    tension sees D2 = d_MT(1.25) and in-plane shear D6 = d_6(1.25).  Matrix
+    tension damage first (sigma~22 = 1.4 Y_T: r_MT = sqrt((1-g) 1.4 + g 1.4^2))
+    leaves r_MC = 1: a later compression is undamaged in 22 (crack
+    closure)."""
+    mat = _poisson_material()
+    lc = 0.3
+    H = _compliance(mat)
+    # fibre compression then tension
+    s, h = oracle.cdm_point(mat, lc, H @ np.array([-1.1 * mat["XC"], 0, 0, 0, 0, 0]), damage_on=True,
+                            plasticity_on=False)
+    assert h[1] == pytest.approx(1.1, rel=1e-12) and h[0] == h[1]
+    eps = np.array([1.0e-3, 0.0, 0.0, 0.0, 0.0, 0.0])
+    s, h2 = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    D1 = _crack_band_damage(1.1, lc, mat["XT"], mat["E1"], mat["GXT"])
+    assert D1 > 0.05
+    assert s == pytest.approx(_damaged_stress(mat, eps, D1, 0.0, 0.0), rel=1e-12, abs=1e-9)
+    # matrix compression then tension and shear
+    _, h = oracle.cdm_point(mat, lc, H @ np.array([0, -1.25 * mat["YC"], 0, 0, 0, 0]), damage_on=True,
+                            plasticity_on=False)
+    assert h[3] == pytest.approx(1.25, rel=1e-12) and h[2] == h[3]
+    assert h[0] == 1.0 and h[1] == 1.0
+    eps = np.array([0.0, 2.0e-3, 0.0, 3.0e-3, 0.0, 0.0])
+    s, h2 = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    assert np.array_equal(h2[:4], h[:4])
+    D2 = _crack_band_damage(1.25, lc, mat["YT"], mat["E2"], mat["GYT"])
+    D6 = _crack_band_damage(1.25, lc, mat["SL"], mat["G12"], mat["GSL"])
+    assert s == pytest.approx(_damaged_stress(mat, eps, 0.0, D2, D6), rel=1e-12, abs=1e-9)
+    assert s[3] == pytest.approx((1 - D6) * mat["G12"] * eps[3], rel=1e-12)
+    # matrix tension first: no carry-over to compression
+    _, h = oracle.cdm_point(mat, lc, H @ np.array([0, 1.4 * mat["YT"], 0, 0, 0, 0]), damage_on=True,
+                            plasticity_on=False)
+    g = mat["GYT"] / mat["GSL"]
+    assert h[2] == pytest.approx(math.sqrt((1 - g) * 1.4 + g * 1.4 ** 2), rel=1e-12) and h[3] == 1.0
+    eps = np.array([0.0, -2.0e-3, 0.0, 0.0, 0.0, 0.0])
+    s, _ = oracle.cdm_point(mat, lc, eps, h, damage_on=True, plasticity_on=False)
+    assert s == pytest.approx(np.linalg.solve(H[:3, :3], eps[:3]).tolist() + [0, 0, 0], rel=1e-12, abs=1e-9)
+
+
 def test_damage_irreversible_and_secant_unloading():
     mat = zero_poisson_material()
     lc = 0.3
