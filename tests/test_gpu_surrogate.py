@@ -167,6 +167,31 @@ def test_impact_with_learned_law(pkg, trained):
     gl.close()
 
 
+def test_learned_law_impact_against_the_oracle(pkg, trained):
+    """The whole impact run with the learned law where it applies (the exact
+    law elsewhere), judged against the FP64 oracle's exact law on the
+    reduced damage plate: peak contact force within 0.5 % of the oracle's
+    and the force history within 1 % of its peak at every step."""
+    s, _, _ = trained
+    w = pi.damage_fp32_plate(nx=32, ny=48, Lx=25.0, Ly=37.5, H=4.4, mass=5.5e-3 / 16, steps=3000)
+    gl = pkg.Solver(w, precision=pkg.PDN_FP32_FORCE)
+    pkg.pdn_set_surrogate(gl.ctx, s, 0.9)
+    o = oracle.model_for(w)
+    for _ in range(30):
+        gl.step(100)
+        assert o.step(100) == 0
+    fl, fo = gl.force_history(), o.force_history()
+    assert len(fl) == len(fo) == 3000 and fo.max() > 0.0
+    pk = abs(fl.max() - fo.max()) / fo.max()
+    hist_err = float(np.abs(fl - fo).max() / fo.max())
+    print(f"\nlearned law vs FP64 oracle: peak {fl.max():.3f} vs {fo.max():.3f} N (rel {pk:.2e}), "
+          f"history err {hist_err:.2e} of peak")
+    assert pk <= 5e-3
+    assert hist_err <= 1e-2
+    gl.close()
+    o.close()
+
+
 def test_empty_training_box_falls_back_to_the_exact_law(pkg, trained):
     """With a training box that contains no point every Gauss point takes the
     exact law: the run follows the exact-law run to FP32 rounding (the two
