@@ -601,6 +601,16 @@ def run_batch(args, ws, rank, local):
     info = pkg.pdn_batch_get_info(b)
     peaks_b = np.array([pkg.pdn_contact_force(c)[1] for c in b.plates])
     repeats_b = sum(pkg.pdn_get_info(c)["n_repeats"] for c in b.plates)
+    hist_b = {}
+    if rank == 0 and not args.no_cpu_baseline:
+        # the force histories of the smallest plates in contact, for the
+        # comparison with the oracle below
+        order = sorted(range(len(cases)), key=lambda k: cases[k].plate.n_hex)
+        for k in order:
+            if peaks_b[k] > 0.0:
+                hist_b[k] = pkg.pdn_contact_force(b.plates[k])[2].copy()
+            if len(hist_b) == 3:
+                break
     b.close()
 
     # the plain step: one context per plate, stepped one after another
@@ -654,6 +664,23 @@ def run_batch(args, ws, rank, local):
         "gpu_launches": int(info["launches"] - info0["launches"]),
         "clocks": clocks.summary(),
     }
+    if hist_b:
+        # the same plates through the FP64 oracle over the same steps from rest
+        import oracle
+        cores = len(os.sched_getaffinity(0))
+        errs = []
+        for k, fb in hist_b.items():
+            o = oracle.model_for(cases[k], n_threads=cores)
+            if o.step(len(fb)) != 0:
+                raise RuntimeError("oracle step failed")
+            fo = o.force_history()
+            o.close()
+            pk = max(float(fo.max()), 1e-300)
+            errs.append({"plate": k, "n_hex": cases[k].plate.n_hex, "steps": len(fb), "f_peak_N_oracle": pk,
+                         "f_peak_rel_err": abs(float(fb.max()) - pk) / pk,
+                         "f_hist_rel_err_max": float(np.abs(fb - fo).max()) / pk})
+        line["batch"]["vs_oracle"] = errs
+        line["batch"]["f_peak_max_rel_err_vs_oracle"] = max(e["f_peak_rel_err"] for e in errs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -45,7 +45,8 @@ extern "C" {
 #define PDN_E_NONFINITE (-4)     /* a nodal acceleration or displacement became NaN/Inf */
 #define PDN_E_RELEASE_LIMIT (-5) /* a step still had adhesive contact nodes after
                                     max_release_iters repetitions (Algorithm 2) */
-#define PDN_E_TIMEOUT (-6)       /* reserved: a bounded device wait gave up */
+#define PDN_E_TIMEOUT (-6)       /* a bounded device wait gave up (the batched launch's
+                                    grid barrier, the learned law's tensor-core wait) */
 #define PDN_E_UNSTABLE (-7)      /* material/mesh gives no stable step (and, for the
                                     learned law, a snap-back length: pdn_surrogate.h) */
 #define PDN_E_STATE (-8)         /* call out of order (e.g. step before set_impactor) */
@@ -260,6 +261,29 @@ int pdn_get_history(pdn_ctx *ctx, void *hist, void *rD);
  * velocity v' = v + dt a instead of a; the value returned is (v' - v)/dt,
  * equal to a up to FP64 rounding.  Host pointer owned by the caller. */
 int pdn_get_acceleration(pdn_ctx *ctx, double *a);
+
+/* Energy ledger at the committed state (Sec. 3.2 reports the energy-time
+ * curves of the impact), evaluated on the device in FP64:
+ *   out[0] kinetic energy of the plate, 1/2 sum_j m_j v_j . v_j with the
+ *          velocity at the committed time level, v + dt/2 a (the stored
+ *          velocity of the scheme is the central-difference one half a step
+ *          back at phi = 1)
+ *   out[1] kinetic energy of the striker, 1/2 M w . w
+ *   out[2] energy stored in the hexes: sum over Gauss points of
+ *          det J * 1/2 sigma : eps_e (ply axes; eps_e the Green strain minus the
+ *          plastic shear strains; sigma the law's nominal stress at the
+ *          committed history, Algorithm 4 -- the secant energy of the damaged
+ *          material)
+ *   out[3] energy stored in the interface elements: sum over Newton-Cotes
+ *          points of 1/2 w tau . Delta (Algorithm 5 at the committed thresholds)
+ *   out[4] work of gravity since the striker was set: sum_j m_j g . d_j +
+ *          M g . (c - c_set)
+ *   out[5] the striker's kinetic energy when it was set (pdn_set_impactor)
+ * For a plate set in motion only by the striker, out[5] + out[4] - (out[0] +
+ * out[1] + out[2] + out[3]) is the energy dissipated by damage, plasticity
+ * and the time integrator: zero up to the integrator's error in an elastic
+ * impact.  Units mJ (N mm).  Host pointer out[6]. */
+int pdn_energies(pdn_ctx *ctx, double out[6]);
 
 /* Nodal internal force f^i ([3][n_nodes]) at the committed state, computed
  * by the same element and gather kernels as a step, without advancing and

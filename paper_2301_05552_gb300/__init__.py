@@ -25,7 +25,7 @@ __all__ = [
     "PdnError", "lib", "build",
     "pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
     "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration",
-    "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
+    "pdn_energies", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "Solver",
     "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
     "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
     "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
@@ -44,7 +44,7 @@ ERRORS = {-1: "PDN_E_ARG", -2: "PDN_E_CUDA", -3: "PDN_E_OOM", -4: "PDN_E_NONFINI
           -5: "PDN_E_RELEASE_LIMIT", -6: "PDN_E_TIMEOUT", -7: "PDN_E_UNSTABLE", -8: "PDN_E_STATE"}
 EXPORTS = ["pdn_init_mesh", "pdn_set_impactor", "pdn_step", "pdn_contact_force", "pdn_damage_field",
            "pdn_get_state", "pdn_set_state", "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration",
-           "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
+           "pdn_energies", "pdn_internal_force", "pdn_get_info", "pdn_profile_kernels", "pdn_destroy", "pdn_last_error", "pdn_internal_force_noalloc",
            "pdn_batch_init", "pdn_batch_plate", "pdn_batch_step", "pdn_batch_get_info",
            "pdn_batch_test_barrier_timeout", "pdn_batch_destroy", "pdn_batch_last_error",
            "pdn_sur_create", "pdn_sur_generate", "pdn_sur_train", "pdn_sur_forward", "pdn_sur_exact",
@@ -140,6 +140,7 @@ def lib():
             L.pdn_get_contact.argtypes = [vp, C.POINTER(C.c_uint8), dp]
             L.pdn_get_history.argtypes = [vp, vp, vp]
             L.pdn_get_acceleration.argtypes = [vp, dp]
+            L.pdn_energies.argtypes = [vp, dp]
             L.pdn_internal_force.argtypes = [vp, dp]
             L.pdn_get_info.argtypes = [vp, C.POINTER(Info)]
             L.pdn_profile_kernels.argtypes = [vp, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_int64)]
@@ -196,7 +197,8 @@ def lib():
             for name in ("pdn_mesh_multiply", "pdn_refined_get_info", "pdn_refined_get", "pdn_init_refined"):
                 getattr(L, name).restype = C.c_int
             for name in ("pdn_set_impactor", "pdn_step", "pdn_damage_field", "pdn_get_state", "pdn_set_state",
-                         "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration", "pdn_internal_force",
+                         "pdn_get_contact", "pdn_get_history", "pdn_get_acceleration", "pdn_energies",
+                         "pdn_internal_force",
                          "pdn_get_info", "pdn_profile_kernels", "pdn_init_mesh"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -387,6 +389,17 @@ def pdn_get_acceleration(ctx: Context):
     a = np.zeros((3, ctx.n_nodes))
     _check(ctx, lib().pdn_get_acceleration(ctx.handle, _ptr(a, C.c_double)))
     return a
+
+
+def pdn_energies(ctx: Context) -> dict:
+    """Energy ledger of the committed state (include/pdn.h), with the
+    dissipated energy derived from it."""
+    out = np.zeros(6)
+    _check(ctx, lib().pdn_energies(ctx.handle, _ptr(out, C.c_double)))
+    d = dict(ke_plate=out[0], ke_striker=out[1], stored_hex=out[2], stored_interface=out[3],
+             work_gravity=out[4], e0_striker=out[5])
+    d["dissipated"] = out[5] + out[4] - (out[0] + out[1] + out[2] + out[3])
+    return d
 
 
 def pdn_internal_force(ctx: Context):

@@ -870,6 +870,10 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
   s.M = mass;
   s.iM = 1.0 / mass;
   s.has = 1;
+  // reference of the energy ledger: the striker's kinetic energy and centre
+  // when it is set (the plate's kinetic and stored energy enter as they are)
+  ctx->imp_e0 = 0.5 * mass * (velocity[0] * velocity[0] + velocity[1] * velocity[1] + velocity[2] * velocity[2]);
+  for (int i = 0; i < 3; ++i) ctx->imp_c0[i] = centre[i];
   PDN_CU(cudaMemcpyAsync(ctx->imp_dev, &s, sizeof(Striker), cudaMemcpyHostToDevice, ctx->stream), "set impactor");
   StrikerStep *ss = ctx->precision == PDN_FP64 ? ctx->Dd.imp_step : ctx->Df.imp_step;
   PDN_CU(launch_striker_init(ctx->imp_dev, ss, ctx->dt, ctx->stream), "striker init");
@@ -957,8 +961,10 @@ int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
     if (rc) return rc;
     const Ctl &c = *ctx->ctl_host;
     if (c.status) {
-      return fail(ctx, c.status, c.status == PDN_E_NONFINITE ? "non-finite acceleration or displacement"
-                                                             : "contact release limit reached (Algorithm 2)");
+      return fail(ctx, c.status,
+                  c.status == PDN_E_NONFINITE  ? "non-finite acceleration or displacement"
+                  : c.status == PDN_E_TIMEOUT ? "a bounded wait on the tensor core gave up (learned law)"
+                                              : "contact release limit reached (Algorithm 2)");
     }
     remaining = target - c.step;
     if (guard > 64 * (ctx->max_repeats + 1)) return fail(ctx, PDN_E_STATE, "step loop made no progress");
@@ -1235,6 +1241,9 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
 // Helpers for other translation units of the library (pdn_noalloc.cu).
 namespace pdn {
 void set_thread_error(const std::string &msg) { g_init_error = msg; }
+int ctx_fail(pdn_ctx *c, int code, const std::string &msg) { return fail(c, code, msg); }
+int ctx_cuda_fail(pdn_ctx *c, cudaError_t e, const char *where) { return cuda_fail(c, e, where); }
+int ctx_read_ctl(pdn_ctx *ctx) { return read_ctl(ctx); }
 template <typename T>
 int fill_mat_public(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_plies, int damage_on,
                     int plasticity_on, std::string &why) {

@@ -22,6 +22,9 @@
 #include "pdn_context.h"
 #include "pdn_device.cuh"
 #include "pdn_internal.h"
+// the items run inside one persistent launch whose earlier phases write the
+// state they read: no read-only data path for that state
+#define PDN_ITEMS_IN_PERSISTENT_KERNEL 1
 #include "pdn_items.cuh"
 
 namespace pdn {

@@ -48,6 +48,8 @@ struct pdn_ctx {
   int max_repeats = 8;
   int64_t hist_cap = 0;
   bool has_imp = false;
+  double imp_e0 = 0.0;                 // striker kinetic energy when set (energy ledger)
+  double imp_c0[3] = {0.0, 0.0, 0.0};  // striker centre when set
   bool tuned = false;
   float tune_ms[12] = {};  // mean internal-force pass time per variant (autotuner)
   cudaGraphExec_t graph = nullptr;

@@ -39,7 +39,7 @@ struct Ctl {
   double time;
   double f_peak;
   int32_t nonfinite;   // set by the gather when an acceleration is not finite
-  int32_t pad;
+  int32_t timeout;     // set by a kernel whose bounded wait on the tensor core gave up
 };
 
 // Rigid striker (Sec. 2.2.2).  The committed part is written only by the tail

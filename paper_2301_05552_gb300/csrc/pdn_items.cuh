@@ -11,6 +11,21 @@
 #include "pdn_device.cuh"
 #include "pdn_internal.h"
 
+// Pointers to state that other blocks write in the course of a pass (the
+// element-precision mirror of the displacement, the Gauss-point history, the
+// interface thresholds).  The per-pass kernels never write these buffers in
+// the launch that reads them through such a pointer, so their loads may take
+// the read-only data path (restrict-qualified pointers).  The batched
+// persistent kernel writes them in earlier phases of the same launch, where a
+// read-only cached line could be stale; it compiles these items with plain
+// pointers by defining PDN_ITEMS_IN_PERSISTENT_KERNEL before including this
+// file.
+#ifdef PDN_ITEMS_IN_PERSISTENT_KERNEL
+#define PDN_STATE_RESTRICT
+#else
+#define PDN_STATE_RESTRICT __restrict__
+#endif
+
 namespace pdn {
 namespace detail {
 
@@ -177,7 +192,7 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
   if (e >= D.nh) return;
   if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, e)) return;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
-  const V4 *__restrict__ U = D.u4[ub];
+  const V4 *PDN_STATE_RESTRICT U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
@@ -203,8 +218,8 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
   const Ctl *ctl = D.ctl;
   const int64_t nh = D.nh;
   const int hb = ctl->hpar;
-  const float *__restrict__ hin = D.hist[hb] + e;
-  float *__restrict__ hout = D.hist[hb ^ 1] + e;
+  const float *PDN_STATE_RESTRICT hin = D.hist[hb] + e;
+  float *PDN_STATE_RESTRICT hout = D.hist[hb ^ 1] + e;
   bool dirty = false;
   float bm[8][3];
   float jd[3], wd[3], vol;
@@ -430,13 +445,13 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
   const int64_t nh = D.nh;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
-  const V4 *__restrict__ U = D.u4[ub];
+  const V4 *PDN_STATE_RESTRICT U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
-  const T *__restrict__ hin = D.hist[hb] + e;
-  T *__restrict__ hout = D.hist[hb ^ 1] + e;
+  const T *PDN_STATE_RESTRICT hin = D.hist[hb] + e;
+  T *PDN_STATE_RESTRICT hout = D.hist[hb ^ 1] + e;
   // An element whose points all still hold the initial history skips the
   // history traffic: it is not read, and written only once a point changes.
   const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][e] != 0;
@@ -638,7 +653,7 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
   const int64_t nc = D.nc;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
-  const V4 *__restrict__ U = D.u4[ub];
+  const V4 *PDN_STATE_RESTRICT U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
   const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + D.nh + c) : 0u;
@@ -694,8 +709,8 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
     e2[1] = e3[2] * e1[0] - e3[0] * e1[2];
     e2[2] = e3[0] * e1[1] - e3[1] * e1[0];
   }
-  const T *__restrict__ rin = D.rD[hb];
-  T *__restrict__ rout = D.rD[hb ^ 1];
+  const T *PDN_STATE_RESTRICT rin = D.rD[hb];
+  T *PDN_STATE_RESTRICT rout = D.rD[hb ^ 1];
   // undamaged interface elements (all r_D = 0) skip the threshold traffic
   const bool pristine_in = D.cflag[0] != nullptr && D.cflag[hb][c] != 0;
   T rv[4];
@@ -1060,7 +1075,10 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     nd += ti[1][k];
   }
   c.nonfinite = 0;  // for the next pass
-  if (mode == MODE_FORCES) {
+  if (c.timeout) {
+    c.status = PDN_E_TIMEOUT;
+    c.mode = MODE_HALT;
+  } else if (mode == MODE_FORCES) {
     c.mode = MODE_DONE;
   } else if (nf) {
     c.status = PDN_E_NONFINITE;

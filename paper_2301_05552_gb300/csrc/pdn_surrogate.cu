@@ -1,8 +1,9 @@
 // Learned surrogate of the intralaminar damage law (include/pdn_surrogate.h):
 // training data from the exact law on the GPU, training (forward, backward,
-// weight gradients, Adam) and inference with BF16 tensor-core kernels
-// (mma.sync m16n8k16, FP32 accumulation), and the hook that lets the hex
-// kernel use it.
+// weight gradients, Adam; warp-level mma.sync m16n8k16 tiles of 16 points)
+// and inference on the Blackwell tensor cores (tcgen05.mma with TMEM
+// accumulators, 128 points per CTA), BF16 operands and FP32 accumulation, and
+// the hook that lets the hex kernel use it.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -390,29 +391,44 @@ __global__ void k_train_update(float *params, float *m1, float *m2, float *grad_
   }
 }
 
-// Inference on raw points: one tile of 16 per warp.
-__global__ void __launch_bounds__(kWarps * 32) k_sur_forward(const float *params, Scaling sc, const float *in,
-                                                             float *out, int64_t n) {
+// Inference on raw points on the Blackwell tensor cores: 128 points per CTA,
+// one per thread (tc_forward128).  A wait on the tensor core that gives up
+// sets *status to PDN_E_TIMEOUT and leaves the CTA's outputs unwritten.
+struct SurTcSmem {
+  UmmaNet N;
+  UmmaTile T;
+};
+constexpr int kTcBlock = kTcRows;
+// dynamic shared memory of the inference kernel, more than it uses: at most
+// three CTAs per SM, so that their TMEM columns (3 x 128) always fit the
+// SM's 512 and no allocation has to wait for another CTA
+constexpr size_t kSurTcSmem = 64 * 1024;
+static_assert(sizeof(SurTcSmem) <= kSurTcSmem, "inference tiles fit the reserved shared memory");
+
+__global__ void __launch_bounds__(kTcBlock) k_sur_forward_tc(const float *params, Scaling sc, const float *in,
+                                                             float *out, int64_t n, int32_t *status) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
-  load_net(N, params);
-  __syncthreads();
-  WarpTiles &W = warp_tiles(smem);
-  const int l = threadIdx.x & 31;
-  const int64_t tile = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (tile * 16 >= n) return;
-  auto idx = [&](int r) -> int64_t {
-    const int64_t i = tile * 16 + r;
-    return i < n ? i : n - 1;
-  };
-  load_inputs(W.a0, in, sc, idx);
-  __syncwarp();
-  warp_forward16(N, W.a0, W.a[0], W.a[1], W.y, kOutPad, nullptr);
-  for (int e = l; e < 16 * kOut; e += 32) {
-    const int r = e / kOut, c = e % kOut;
-    const int64_t i = tile * 16 + r;
-    if (i < n) out[i * kOut + c] = W.y[r * kOutPad + c] * sc.out_mul[c] + sc.out_shift[c];
+  SurTcSmem &S = *reinterpret_cast<SurTcSmem *>(smem);
+  const int t = threadIdx.x;
+  load_net_umma(S.N, params);
+  const int64_t i = (int64_t)blockIdx.x * kTcBlock + t;
+  float xn[kInPad];
+#pragma unroll
+  for (int c = 0; c < kInPad; ++c) {
+    const float raw = (c < kIn && i < n) ? in[i * kIn + c] : 0.0f;
+    xn[c] = c < kIn ? (raw - sc.in_shift[c]) * sc.in_mul[c] : 0.0f;
   }
+  tc_store_input(S.T, t, xn);
+  tc_setup(S.T);
+  uint32_t phase = 0;
+  float y[kOutPad];
+  const bool ok = tc_forward128(S.N, S.T, phase, y);
+  if (ok && i < n) {
+#pragma unroll
+    for (int c = 0; c < kOut; ++c) out[i * kOut + c] = y[c] * sc.out_mul[c] + sc.out_shift[c];
+  }
+  if (!ok && t == 0) atomicExch(status, PDN_E_TIMEOUT);
+  tc_teardown(S.T);
 }
 
 // He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases.
@@ -437,41 +453,43 @@ __global__ void k_init_params(float *p, uint64_t seed) {
 // first, then either the network (all loading-function ratios at most the
 // context's onset ratio and every input inside the training box: the
 // thresholds do not change there) or the exact damage part.  The network
-// runs once per point index for the 32 points of a warp (two 16-point tiles)
-// whenever any lane needs it; lanes past the last element follow the same
-// control flow on a valid element and store nothing.
+// runs on the tensor cores (tcgen05, TMEM accumulators) for the 128 points of
+// the CTA (one element per thread, the same Gauss point) whenever any thread
+// of the CTA needs it; threads past the last element follow the same control
+// flow on a valid element and store nothing.  A bounded wait on the tensor
+// core that gives up raises the control block's timeout word (the tail then
+// halts the run with PDN_E_TIMEOUT) and the CTA finishes with the exact law.
 
-struct HexSurTiles {
-  __nv_bfloat16 x[2][16 * kS16];
-  __nv_bfloat16 h0[16 * kS64], h1[16 * kS64];
-  float y[2][16 * kOutPad];
+constexpr int kHexSurBlock = kTcRows;  // at most three CTAs per SM (registers): 3 x 128 TMEM columns
+struct HexSurSmem {
+  UmmaNet N;
+  UmmaTile T;
+  Scaling sc;
 };
-constexpr int kHexSurBlock = 128;
-constexpr size_t kHexSurSmem = sizeof(SmemNet) + sizeof(Scaling) + (kHexSurBlock / 32) * sizeof(HexSurTiles);
+constexpr size_t kHexSurSmem = sizeof(HexSurSmem);
 static_assert(sizeof(Scaling) == PDN_SUR_SCALING * sizeof(float), "scaling record of 60 floats");
 static_assert(sizeof(SmemNet) % 16 == 0 && sizeof(Scaling) % 16 == 0, "16-byte aligned shared tiles");
 
-__global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<float> M) {
+__global__ void __launch_bounds__(kHexSurBlock, 3) k_hex_sur(Dev<float> D, Mat<float> M) {
   extern __shared__ __align__(16) unsigned char smem[];
-  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
-  Scaling &sc = *reinterpret_cast<Scaling *>(smem + sizeof(SmemNet));
-  HexSurTiles &Wt = reinterpret_cast<HexSurTiles *>(smem + sizeof(SmemNet) + sizeof(Scaling))[threadIdx.x >> 5];
+  HexSurSmem &S = *reinterpret_cast<HexSurSmem *>(smem);
   const Ctl *ctl = D.ctl;
   const int mode = ctl->mode;
   if (mode >= MODE_DONE) return;
-  load_net(N, D.sur_params);
+  load_net_umma(S.N, D.sur_params);
   for (int k = threadIdx.x; k < PDN_SUR_SCALING; k += blockDim.x)
-    reinterpret_cast<float *>(&sc)[k] = D.sur_params[kNumParams + k];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
+    reinterpret_cast<float *>(&S.sc)[k] = D.sur_params[kNumParams + k];
+  const Scaling &sc = S.sc;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nh = D.nh;
-  if (e - lane >= nh) return;  // the whole warp is past the last element
   // a repeated pass evaluates only the marked elements (local repetition);
-  // the others follow the warp on their own element and store nothing
+  // the others follow the CTA on their own element and store nothing
   bool act = e < nh;
   if (mode == MODE_REPEAT && act) act = repeat_take(D.rmark_e, e);
-  if (!__any_sync(0xffffffffu, act)) return;
+  if (!__syncthreads_or(act)) return;  // nothing to do in this CTA (no TMEM held yet)
+  tc_setup(S.T);
+  uint32_t phase = 0;
+  bool tc_ok = true;
   const int64_t el = e < nh ? e : nh - 1;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
@@ -514,7 +532,6 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
 #pragma unroll
   for (int m = 0; m < 8; ++m) C[m][0] = C[m][1] = C[m][2] = 0.0f;
   const float gp = 0.57735026918962576451f;
-  const int tl = lane >> 4, row = lane & 15;
 #pragma unroll 1
   for (int g = 0; g < 8; ++g) {
     float h[7];
@@ -551,29 +568,24 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
     for (int k = 0; k < 4; ++k) inbox = inbox && h[k] >= sc.lo[6 + k] && h[k] <= sc.hi[6 + k];
     const bool use = act && inbox && cdm_onset_ratio2(M, L, eel, h) <= D.sur_ratio2;
     float sm[6];
-    if (__any_sync(0xffffffffu, use)) {
-      __nv_bfloat16 *xr = Wt.x[tl] + row * kS16;
+    bool net = false;
+    if (__syncthreads_or(use) && tc_ok) {
+      float xn[kInPad];
 #pragma unroll
-      for (int c = 0; c < kInPad; c += 2) {
-        float v[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int cc = c + q;
-          const float raw = cc < 6 ? eel[cc] : (cc < kIn ? h[cc - 6] : 0.0f);
-          v[q] = cc < kIn ? (raw - sc.in_shift[cc]) * sc.in_mul[cc] : 0.0f;
-        }
-        *reinterpret_cast<__nv_bfloat162 *>(xr + c) = __floats2bfloat162_rn(v[0], v[1]);
+      for (int c = 0; c < kInPad; ++c) {
+        const float raw = c < 6 ? eel[c] : (c < kIn ? h[c - 6] : 0.0f);
+        xn[c] = c < kIn ? (raw - sc.in_shift[c]) * sc.in_mul[c] : 0.0f;
       }
-      __syncwarp();
-      warp_forward16(N, Wt.x[0], Wt.h0, Wt.h1, Wt.y[0], kOutPad, nullptr);
-      warp_forward16(N, Wt.x[1], Wt.h0, Wt.h1, Wt.y[1], kOutPad, nullptr);
-      if (use) {
+      tc_store_input(S.T, threadIdx.x, xn);
+      float y[kOutPad];
+      tc_ok = tc_forward128(S.N, S.T, phase, y);
+      net = use && tc_ok;
+      if (net) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) sm[k] = Wt.y[tl][row * kOutPad + k] * sc.out_mul[k] + sc.out_shift[k];
+        for (int k = 0; k < 6; ++k) sm[k] = y[k] * sc.out_mul[k] + sc.out_shift[k];
       }
-      __syncwarp();
     }
-    if (!use) cdm_damage(M, L, (const float(*)[3]) nullptr, vol, lc, ep, h, sm);
+    if (!net) cdm_damage(M, L, (const float(*)[3]) nullptr, vol, lc, ep, h, sm);
     if (act) {
       if (!pristine_in) {
 #pragma unroll
@@ -593,19 +605,19 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
         }
       }
     }
-    float S[3][3];
-    S[0][0] = c2 * sm[0] - 2.0f * csn * sm[3] + s2 * sm[1];
-    S[1][1] = s2 * sm[0] + 2.0f * csn * sm[3] + c2 * sm[1];
-    S[2][2] = sm[2];
-    S[0][1] = S[1][0] = csn * sm[0] + (c2 - s2) * sm[3] - csn * sm[1];
-    S[0][2] = S[2][0] = cs * sm[4] - sn * sm[5];
-    S[1][2] = S[2][1] = sn * sm[4] + cs * sm[5];
+    float Sg[3][3];
+    Sg[0][0] = c2 * sm[0] - 2.0f * csn * sm[3] + s2 * sm[1];
+    Sg[1][1] = s2 * sm[0] + 2.0f * csn * sm[3] + c2 * sm[1];
+    Sg[2][2] = sm[2];
+    Sg[0][1] = Sg[1][0] = csn * sm[0] + (c2 - s2) * sm[3] - csn * sm[1];
+    Sg[0][2] = Sg[2][0] = cs * sm[4] - sn * sm[5];
+    Sg[1][2] = Sg[2][1] = sn * sm[4] + cs * sm[5];
     float Q[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
       for (int I = 0; I < 3; ++I)
-        Q[k][I] = wd[k] * (S[k][I] + S[k][0] * H[I][0] + S[k][1] * H[I][1] + S[k][2] * H[I][2]);
+        Q[k][I] = wd[k] * (Sg[k][I] + Sg[k][0] * H[I][0] + Sg[k][1] * H[I][1] + Sg[k][2] * H[I][2]);
 #pragma unroll
     for (int I = 0; I < 3; ++I) {
       C[1][I] += Q[0][I];
@@ -617,6 +629,8 @@ __global__ void __launch_bounds__(kHexSurBlock) k_hex_sur(Dev<float> D, Mat<floa
       C[7][I] += et * ze * Q[0][I] + xi * ze * Q[1][I] + xi * et * Q[2][I];
     }
   }
+  tc_teardown(S.T);
+  if (!tc_ok && threadIdx.x == 0) atomicOr(&D.ctl->timeout, 1);
   if (!act) return;
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][el] = (pristine_in && !dirty) ? 1 : 0;
@@ -661,6 +675,7 @@ struct pdn_surrogate {
   TrainBufs tb{};
   float *partW = nullptr, *partB = nullptr, *grad = nullptr;
   double *loss_dev = nullptr;
+  int32_t *status_dev = nullptr;  // error word of the tensor-core inference kernel
   std::string err;
 };
 
@@ -773,6 +788,7 @@ void pdn_sur_destroy(pdn_surrogate *s) {
   cudaFree(s->Y);
   cudaFree(s->grad);
   cudaFree(s->loss_dev);
+  cudaFree(s->status_dev);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   cudaSetDevice(prev);
   delete s;
@@ -832,14 +848,16 @@ static int pdn_sur_create_body(pdn_surrogate **out, const pdn_material *mat, dou
       cudaMalloc(&s->m1, sizeof(float) * kNumParams) != cudaSuccess ||
       cudaMalloc(&s->m2, sizeof(float) * kNumParams) != cudaSuccess ||
       cudaMalloc(&s->grad, sizeof(float) * kNumParams) != cudaSuccess ||
-      cudaMalloc(&s->loss_dev, sizeof(double) * 1) != cudaSuccess)
+      cudaMalloc(&s->loss_dev, sizeof(double) * 1) != cudaSuccess ||
+      cudaMalloc(&s->status_dev, sizeof(int32_t)) != cudaSuccess)
     return bad(PDN_E_OOM, "surrogate parameters");
   cudaMemsetAsync(s->m1, 0, sizeof(float) * kNumParams, s->stream);
   cudaMemsetAsync(s->m2, 0, sizeof(float) * kNumParams, s->stream);
   k_init_params<<<(kNumParams + 255) / 256, 256, 0, s->stream>>>(s->params, seed);
   if (cudaFuncSetAttribute(k_train_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_sur_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) != cudaSuccess)
+      cudaFuncSetAttribute(k_sur_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSurTcSmem) !=
+          cudaSuccess)
     return bad(PDN_E_CUDA, "shared-memory attribute");
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bad(PDN_E_CUDA, "surrogate init");
   *out = s;
@@ -1035,17 +1053,21 @@ static int sur_points(pdn_surrogate *s, const float *in, float *out, int64_t n, 
   if (exact) {
     k_law_points<<<(unsigned)((n + 127) / 128), 128, 0, s->stream>>>(s->law, din, dout, n);
   } else {
-    const int64_t tiles = (n + 15) / 16;
-    k_sur_forward<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, kTileSmem, s->stream>>>(s->params, s->sc,
-                                                                                                    din, dout, n);
+    cudaMemsetAsync(s->status_dev, 0, sizeof(int32_t), s->stream);
+    k_sur_forward_tc<<<(unsigned)((n + kTcBlock - 1) / kTcBlock), kTcBlock, kSurTcSmem, s->stream>>>(
+        s->params, s->sc, din, dout, n, s->status_dev);
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && !on_device)
     e = cudaMemcpyAsync(out, dout, sizeof(float) * kOut * n, cudaMemcpyDeviceToHost, s->stream);
+  int32_t st = 0;
+  if (e == cudaSuccess && !exact)
+    e = cudaMemcpyAsync(&st, s->status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   cudaFree(tmp_in);
   cudaFree(tmp_out);
   if (e != cudaSuccess) return scuda(s, e, exact ? "exact law" : "surrogate forward");
+  if (st) return sfail(s, st, "surrogate forward: a bounded wait on the tensor core gave up");
   return PDN_OK;
 }
 

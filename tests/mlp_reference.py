@@ -71,3 +71,15 @@ def forward(p, xn):
     a = np.maximum(a @ W2.T + b2, 0.0)
     a = np.maximum(a @ W3.T + b3, 0.0)
     return a @ W4.T + b4
+
+
+def forward_bf16(p, xn):
+    """Forward pass with the operands of the tensor-core products rounded to
+    bfloat16 (weights, the input, each hidden activation after the ReLU),
+    sums and biases in FP64."""
+    W1, b1, W2, b2, W3, b3, W4, b4 = unpack(p)
+    a = bf16(xn)
+    a = bf16(np.maximum(a @ bf16(W1).T + b1, 0.0))
+    a = bf16(np.maximum(a @ bf16(W2).T + b2, 0.0))
+    a = bf16(np.maximum(a @ bf16(W3).T + b3, 0.0))
+    return a @ bf16(W4).T + b4

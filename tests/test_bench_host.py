@@ -64,6 +64,23 @@ def test_algorithmic_bytes_of_the_benchmark_plate():
         393216 * 481 + 344064 * 64 + 771807 * 141 + 24897 * 48)
 
 
+def test_algorithmic_bytes_of_a_loaded_window():
+    """The 400x600x32 plate in its loaded window: per hex 32 B connectivity,
+    1 B ply, the pristine flag read and written (2 B), history bytes (448 B)
+    only for the elements that left the initial state; per node 24 B."""
+    assert bench.hex_alg_bytes_state(7680000, 11327047, 145) == (
+        7680000 * 35 + 145 * 448 + 11327047 * 24) == 540714088
+    assert bench.step_alg_bytes_state(393216, 8, 344064, 0, 771807, 24897) == (
+        393216 * 35 + 8 * 448 + 344064 * 34 + 771807 * 141 + 24897 * 48)
+
+
+def test_issue_bound_of_a_launch():
+    """566.0 M warp instructions at 2,070 MHz on 152 SMs with four
+    schedulers each: 0.450 ms."""
+    assert bench.issue_bound_ms(566001765, 2070.0) == pytest.approx(566001765 / (152 * 4 * 2.07e9) * 1e3)
+    assert bench.issue_bound_ms(566001765, 2070.0) == pytest.approx(0.4497, abs=1e-4)
+
+
 def test_algorithmic_bytes_of_one_division():
     """The AS4/8552 coupon divided once: coarse mesh read once, divided mesh
     written once (25 B per node, 33 B per hex, 32 B per interface, 4 B per

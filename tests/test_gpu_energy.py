@@ -1,0 +1,124 @@
+"""Energy ledger of the device (pdn_energies), Sec. 3.2's energy-time view of
+the impact.
+
+* 40x40x4 mm plain plate (FP64, elastic), full 2,000-step impact: every term
+  equals the FP64 oracle's at the same state (kinetic energy of plate and
+  striker at the committed time level, strain energy), and the balance
+  striker energy = plate kinetic + striker kinetic + strain closes to 1 % of
+  the striker's initial energy (the oracle's own pin).
+* 100x150x4.4 mm plate, 128x192x16 hex8 with interfaces, elastic (damage and
+  plasticity off), FP32 elements: in free vibration (striker far away) the
+  ledger's total stays constant (no drift); through the first 2,000 steps of
+  the impact the plate and striker energies account for the striker's loss
+  up to the contact projection's inelastic node capture, which only removes
+  energy.
+* The same plate with damage on, through the peak force: the dissipated
+  energy is positive and grows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import pdn_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2301_05552_gb300 as p
+    p.lib()
+    return p
+
+
+def test_plain_plate_ledger_matches_oracle_and_balances(pkg):
+    w = pi.plain_fp64_plate()
+    g = pkg.Solver(w)
+    o = oracle.model_for(w)
+    g.step(w.steps)
+    assert o.step(w.steps) == 0
+    eg = pkg.pdn_energies(g.ctx)
+    eo = o.energies()
+    d, v, a = o.state()
+    dt = o.info()["dt"]
+    m = o.mass()
+    vi = v + 0.5 * dt * a
+    ke_o = 0.5 * float((m * vi * vi).sum())
+    assert eg["ke_plate"] == pytest.approx(ke_o, rel=1e-6)
+    assert eg["ke_striker"] == pytest.approx(eo["ke_striker"], rel=1e-9)
+    assert eg["stored_hex"] == pytest.approx(eo["strain"], rel=1e-6)
+    assert eg["stored_interface"] == 0.0 and eg["work_gravity"] == 0.0
+    e0 = 0.5 * w.mass * w.speed ** 2
+    assert eg["e0_striker"] == pytest.approx(e0, rel=1e-14)
+    total = eg["ke_plate"] + eg["ke_striker"] + eg["stored_hex"]
+    print(f"\nplain plate ledger: plate KE {eg['ke_plate']:.4f}, striker KE {eg['ke_striker']:.4f}, "
+          f"strain {eg['stored_hex']:.4f}, e0 {e0:.4f} mJ, balance {(total - e0) / e0:.2e}")
+    assert total == pytest.approx(e0, rel=1e-2)
+    g.close()
+    o.close()
+
+
+def _elastic_plate():
+    import dataclasses
+    w = pi.damage_fp32_plate()
+    return dataclasses.replace(w, damage_on=False, plasticity_on=False)
+
+
+def test_elastic_damage_plate_free_vibration_keeps_its_energy(pkg):
+    w = _elastic_plate()
+    g = pkg.Solver(w)
+    r, m, c, v = w.impactor()
+    pkg.pdn_set_impactor(g.ctx, r, m, (c[0], c[1], c[2] + 1000.0), (0.0, 0.0, -1.0))
+    d0, v0 = pi.seeded_state(w.plate, 5, amp=2e-3, vamp=0.0)
+    pkg.pdn_set_state(g.ctx, d0, v0)
+
+    def plate_energy():
+        e = pkg.pdn_energies(g.ctx)
+        return e["ke_plate"] + e["stored_hex"] + e["stored_interface"]
+
+    E0 = plate_energy()
+    dev = []
+    for _ in range(20):
+        g.step(50)
+        dev.append((plate_energy() - E0) / E0)
+    dev = np.array(dev)
+    print(f"\nfree vibration of the 128x192x16 plate: energy {E0:.4e} mJ, deviation max {np.abs(dev).max():.2e}, "
+          f"drift {dev[10:].mean() - dev[:10].mean():.2e}")
+    assert E0 > 0.0
+    assert np.abs(dev).max() < 3e-2
+    assert abs(dev[10:].mean() - dev[:10].mean()) < 2e-3
+    g.close()
+
+
+def test_elastic_damage_plate_impact_balance(pkg):
+    w = _elastic_plate()
+    g = pkg.Solver(w)
+    rows = []
+    for _ in range(10):
+        g.step(200)
+        e = pkg.pdn_energies(g.ctx)
+        plate = e["ke_plate"] + e["stored_hex"] + e["stored_interface"]
+        rows.append((plate, e["dissipated"]))
+    plate, diss = rows[-1]
+    print(f"\nelastic 128x192x16 plate, 2000 steps: plate energy {plate:.4f} mJ, striker loss minus plate gain "
+          f"{diss:.4f} mJ ({diss / plate:.2e} of the plate's)")
+    assert plate > 0.0
+    # the contact projection captures nodes inelastically: energy can only leave
+    assert all(d >= -1e-3 * max(p, 1e-9) for p, d in rows)
+    assert diss <= 5e-2 * plate
+    g.close()
+
+
+def test_damage_plate_dissipates_energy(pkg):
+    w = pi.damage_fp32_plate()
+    g = pkg.Solver(w)
+    diss = []
+    for _ in range(6):
+        g.step(1000)
+        diss.append(pkg.pdn_energies(g.ctx)["dissipated"])
+    e = pkg.pdn_energies(g.ctx)
+    print(f"\ndamage plate, 6000 steps: dissipated {['%.3f' % x for x in diss]} mJ, plate KE {e['ke_plate']:.3f}, "
+          f"hex {e['stored_hex']:.3f}, interfaces {e['stored_interface']:.3f}")
+    assert diss[-1] > 0.0
+    assert diss[-1] > diss[1]
+    g.close()

@@ -64,6 +64,30 @@ def test_gradient_matches_fp64_backprop(pkg):
     s.close()
 
 
+def test_tensor_core_forward_matches_fp64_reference(pkg):
+    """Inference on the Blackwell tensor cores (tcgen05, TMEM accumulators,
+    128 points per CTA; 1,000 points leave a partial last CTA) against the
+    FP64 forward pass with the same bf16 rounding points, and against plain
+    FP64 to the bf16 precision, for the initial and a perturbed network."""
+    s = pkg.pdn_sur_create(_mat(), LC, seed=7)
+    p, sc = pkg.pdn_sur_get_params(s)
+    rng = np.random.default_rng(4)
+    for trial in range(2):
+        if trial == 1:
+            p = (p + rng.normal(scale=0.05, size=p.shape)).astype(np.float32)
+            pkg.pdn_sur_set_params(s, p, sc)
+        x = rng.normal(size=(1000, 10)).astype(np.float32)
+        y = pkg.pdn_sur_forward(s, x).astype(np.float64)
+        xn = (x.astype(np.float64) - sc[0:10]) * sc[10:20]
+        yb = R.forward_bf16(p.astype(np.float64), xn) * sc[30:40] + sc[20:30]
+        y64 = R.forward(p.astype(np.float64), xn) * sc[30:40] + sc[20:30]
+        scale = np.abs(yb).max()
+        assert np.abs(y - yb).max() <= 1e-2 * scale
+        assert np.sqrt(np.mean((y - yb) ** 2)) <= 1e-3 * scale
+        assert np.abs(y - y64).max() <= 5e-2 * scale
+    s.close()
+
+
 def test_exact_law_matches_oracle_point_law(pkg):
     s = pkg.pdn_sur_create(_mat(), LC, seed=0)
     rng = np.random.default_rng(2)
