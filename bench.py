@@ -884,9 +884,10 @@ def run_surrogate(args, ws, rank, local):
         g.close()
     s.close()
     ex, le = runs["exact"], runs["learned"]
-    # tensor-core work of the learned-law hex kernel: every Gauss point of
-    # every warp that needs the network runs it (padded 16-wide input and
-    # output layers): 2 * (16*64 + 2*64*64 + 64*16) flops per point
+    # tensor-core work of the learned-law hex kernel, counted as if every
+    # Gauss point ran the network (padded 16-wide input and output layers):
+    # 2 * (16*64 + 2*64*64 + 64*16) flops per point; a CTA runs it for its
+    # 128 points whenever one of them needs it
     flops = plate.n_hex * 8 * 2 * (16 * 64 + 2 * 64 * 64 + 64 * 16)
     peak_tf = 1900.8
     try:
@@ -900,7 +901,8 @@ def run_surrogate(args, ws, rank, local):
         "vs_baseline": None, "dtype": "bf16 (network) + f32 + f64", "data": "synthetic",
         "config": {"workload": w.name + "_learned_law", "n_hex": plate.n_hex, "n_coh": plate.n_coh,
                    "n_nodes": plate.n_nodes, "l2": "inputs larger than L2", "onset_ratio": 0.9,
-                   "network": "10-64-64-64-10 ReLU, BF16 weights, FP32 accumulation (mma.sync m16n8k16)"},
+                   "network": "10-64-64-64-10 ReLU, BF16 weights, FP32 accumulation (tcgen05.mma, TMEM "
+                              "accumulators, 128 points per CTA)"},
         "surrogate": {
             "speedup_vs_exact_law": ex["ms"] / le["ms"], "exact_ms_per_step": ex["ms"] / K,
             "exact_value": plate.n_hex * K / (ex["ms"] * 1e-3),

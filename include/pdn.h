@@ -167,9 +167,21 @@ typedef struct {
                               targets (never chosen by the autotuner, which times
                               0..3).  The environment variable PDN_HEX_VARIANT
                               (0..7) fixes it instead (no timing, tune_ms 0) */
-  int32_t reserved;
+  int32_t sweep;           /* 0: separate element, interface and gather kernels; 1, 2, 3:
+                              the column sweep (FP32 box hexes, flat interfaces, a plate
+                              layered as a full grid of columns) with tiles of 16 x 8,
+                              8 x 8 or 8 x 4 columns: one kernel evaluates the elements
+                              layer by layer and updates every node inside a tile from
+                              shared memory; only tile-boundary nodes go through the
+                              element-force slots.  Planned by pdn_init_mesh where the
+                              mesh allows it and kept by the autotuner of the first
+                              pdn_step when it is faster.  The environment variable
+                              PDN_SWEEP=0, read by pdn_init_mesh, keeps the separate
+                              kernels */
   double tune_ms[12];      /* mean time of an internal-force pass with each variant when
-                              tuned (0 if not; entries 8..11 unused) */
+                              tuned (0 if not): entries 0..3 the hex variants with separate
+                              kernels, entry 8 the column sweep (0 where none was planned);
+                              the fastest is used.  Entries 4..7, 9..11 unused */
 } pdn_info;
 
 /* Create a context on the current CUDA device: validate and copy the mesh,

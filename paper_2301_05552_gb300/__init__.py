@@ -96,7 +96,7 @@ class Info(C.Structure):
                 ("f_peak", C.c_double), ("step", C.c_int64), ("n_active", C.c_int64), ("n_repeats", C.c_int64),
                 ("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
                 ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32),
-                ("hex_variant", C.c_int32), ("reserved", C.c_int32), ("tune_ms", C.c_double * 12)]
+                ("hex_variant", C.c_int32), ("sweep", C.c_int32), ("tune_ms", C.c_double * 12)]
 
 
 class BatchInfo(C.Structure):

@@ -278,6 +278,102 @@ void hex_gauss(const double X[8][3], double detJ[8], double N[8][8]) {
 
 namespace {
 
+// Column sweep plan (pdn_internal.h, Sweep) of a layered plate: every hex
+// layer and interface layer is a full nx x ny grid of columns numbered x
+// fastest, nodes are numbered node layer by node layer (x fastest), element
+// layer s joins node layers b and b + 1, and the layers chain from the bottom
+// node layer to the top one.  Checked element by element; false (no sweep)
+// for any other mesh.  The tile shape and the z-chunks give enough blocks to
+// fill the GPU; bnodes lists the nodes on tile and chunk boundaries, which the
+// gather over the list updates.
+bool plan_sweep(int64_t nn, int64_t nh, int64_t nc, const int32_t *hex, const int32_t *coh, int n_sm, Sweep &S,
+                std::vector<int32_t> &bnodes) {
+  if (nh < 1) return false;
+  const int64_t nxn = (int64_t)hex[3] - hex[0];
+  const int64_t per_layer = (int64_t)hex[4] - hex[0];
+  if (hex[0] != 0 || hex[1] != 1 || nxn < 2 || per_layer <= 0 || per_layer % nxn != 0) return false;
+  const int64_t nx = nxn - 1, nyn = per_layer / nxn, ny = nyn - 1;
+  const int64_t cols = nx * ny;
+  if (ny < 1 || nh % cols != 0 || nc % cols != 0 || nn % per_layer != 0) return false;
+  const int64_t n_hl = nh / cols, n_cl = nc / cols, n_nl = nn / per_layer;
+  const int64_t n_st = n_hl + n_cl;
+  if (n_st > kMaxStages || n_st != n_nl - 1) return false;
+  // layer of each element layer; every element checked against the pattern
+  std::vector<int32_t> stage_of_bottom(n_nl, -1);
+  std::vector<int32_t> kind(n_st), base(n_st), bot(n_st);
+  auto check_layer = [&](const int32_t *conn, int64_t first, int k, int kd) {
+    const int64_t b = conn[8 * first] / per_layer;
+    if (conn[8 * first] != b * per_layer || conn[8 * first + 4] != (b + 1) * per_layer) return false;
+    for (int64_t r = 0; r < cols; ++r) {
+      const int64_t i = r % nx, j = r / nx, n00 = j * nxn + i;
+      const int32_t *q = conn + 8 * (first + r);
+      const int64_t want[4] = {n00, n00 + 1, n00 + 1 + nxn, n00 + nxn};
+      for (int a = 0; a < 4; ++a)
+        if (q[a] != b * per_layer + want[a] || q[a + 4] != (b + 1) * per_layer + want[a]) return false;
+    }
+    if (b < 0 || b >= n_nl - 1 || stage_of_bottom[b] >= 0) return false;
+    stage_of_bottom[b] = k;
+    kind[k] = kd;
+    base[k] = (int32_t)first;
+    bot[k] = (int32_t)b;
+    return true;
+  };
+  for (int64_t s = 0; s < n_hl; ++s)
+    if (!check_layer(hex, s * cols, (int)s, 0)) return false;
+  for (int64_t s = 0; s < n_cl; ++s)
+    if (!check_layer(coh, s * cols, (int)(n_hl + s), 1)) return false;
+  // stages bottom to top
+  S = Sweep{};
+  S.nx = (int32_t)nx;
+  S.ny = (int32_t)ny;
+  S.nxn = (int32_t)nxn;
+  S.n_stages = (int32_t)n_st;
+  S.per_layer = per_layer;
+  for (int64_t L = 0; L < n_nl - 1; ++L) {
+    const int k = stage_of_bottom[L];
+    if (k < 0) return false;
+    S.kind[L] = kind[k];
+    S.base[L] = base[k];
+    S.bot[L] = bot[k];
+  }
+  // tile shape and z-chunks: at least eight blocks per SM in total
+  static const int TXS[3] = {16, 8, 8}, TYS[3] = {8, 8, 4};
+  const int64_t want = (int64_t)8 * n_sm;
+  int t = 2;
+  for (int c = 0; c < 3; ++c) {
+    const int64_t tiles = ((nx + TXS[c] - 1) / TXS[c]) * ((ny + TYS[c] - 1) / TYS[c]);
+    if (tiles >= want) {
+      t = c;
+      break;
+    }
+  }
+  S.tile = t;
+  S.tiles_x = (int32_t)((nx + TXS[t] - 1) / TXS[t]);
+  S.tiles_y = (int32_t)((ny + TYS[t] - 1) / TYS[t]);
+  const int64_t tiles = (int64_t)S.tiles_x * S.tiles_y;
+  int64_t chunks = std::max<int64_t>(1, (want + tiles - 1) / tiles);
+  chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, n_st / 4));  // at least four stages per chunk
+  S.chunk_len = (int32_t)((n_st + chunks - 1) / chunks);
+  S.chunks = (int32_t)((n_st + S.chunk_len - 1) / S.chunk_len);
+  // boundary nodes: tile-boundary columns of every node layer, and every
+  // column of the node layers shared by two z-chunks
+  std::vector<uint8_t> bcol((size_t)per_layer, 0);
+  for (int64_t j = 0; j <= ny; ++j)
+    for (int64_t i = 0; i <= nx; ++i)
+      bcol[j * nxn + i] = ((i > 0 && i < nx && i % TXS[t] == 0) || (j > 0 && j < ny && j % TYS[t] == 0)) ? 1 : 0;
+  bnodes.clear();
+  for (int64_t L = 0; L < n_nl; ++L) {
+    const bool shared = L % S.chunk_len == 0 && L > 0 && L < n_st;
+    for (int64_t q = 0; q < per_layer; ++q)
+      if (shared || bcol[q]) bnodes.push_back((int32_t)(L * per_layer + q));
+  }
+  return true;
+}
+
+}  // namespace
+
+namespace {
+
 // The history of an element (interface element) flagged pristine is not
 // maintained in the buffers; it is the initial history (r = 1, plastic
 // strain 0; interface r_D = 0), which is what is returned for it.
@@ -536,6 +632,23 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       rank[e] = w;
     }
   }
+  // column sweep (FP32 box hexes, flat interfaces, eight slots per node);
+  // PDN_SWEEP=0, read here, keeps separate element and gather kernels
+  Sweep sweep{};
+  std::vector<int32_t> bnodes;
+  bool sweep_on = false;
+  {
+    const char *sv = std::getenv("PDN_SWEEP");
+    const bool allowed = !(sv && sv[0] == '0' && sv[1] == '\0');
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) {
+      cudaGetLastError();
+      n_sm = 1;
+    }
+    if (allowed && opt->precision == PDN_FP32_FORCE && all_boxes && all_flat_coh && ell)
+      sweep_on = plan_sweep(nn, nh, nc, mesh->hex, mesh->coh, n_sm, sweep, bnodes);
+  }
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
   double dtc = INFINITY;
@@ -587,7 +700,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   const bool fp64 = ctx->precision == PDN_FP64;
   const size_t ts = fp64 ? 8 : 4;
   struct Ptrs {
-    int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos, *act_cnt;
+    int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos, *act_cnt, *bnodes;
     uint32_t *rank;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
@@ -640,6 +753,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     P.fhist = A.take<double>(sizeof(double) * ctx->hist_cap);
     P.fout = A.take<double>(sizeof(double) * 3 * nn);
     P.field = A.take<float>(sizeof(float) * std::max(nh, nc1));
+    P.bnodes = A.take<int32_t>(sizeof(int32_t) * std::max<size_t>(bnodes.size(), 1));
   };
   Arena probe;
   layout(probe);
@@ -726,6 +840,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   chk(up(d_col, col.data(), sizeof(int32_t) * col.size()));
   chk(up(P.pos, pos.data(), sizeof(int32_t) * pos.size()));
   chk(up(P.rank, rank.data(), sizeof(uint32_t) * rank.size()));
+  if (sweep_on) chk(up(P.bnodes, bnodes.data(), sizeof(int32_t) * bnodes.size()));
   chk(up(d_mass, mass.data(), sizeof(double) * nn));
   chk(up(d_imass, imass.data(), imass.size()));
   for (int b = 0; b < 2; ++b) {
@@ -805,8 +920,11 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     // again (the reference for the local repetition, same results)
     const char *fr = std::getenv("PDN_FULL_REPEAT");
     const bool full = fr != nullptr && fr[0] == '1' && fr[1] == '\0';
-    D.rmark_e = full ? nullptr : d_rmark_e;
-    D.rmark_n = full ? nullptr : d_rmark_n;
+    // the column sweep evaluates every element and node again in a repeated
+    // pass (the same results as the local repetition)
+    D.rmark_e = (full || sweep_on) ? nullptr : d_rmark_e;
+    D.rmark_n = (full || sweep_on) ? nullptr : d_rmark_n;
+    D.sweep = nullptr;
     D.nrm = d_nrm;
     D.lam = d_lam;
     D.trial = d_trial;
@@ -831,6 +949,18 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     wire(ctx->Dd, double{});
   else
     wire(ctx->Df, float{});
+  ctx->rmark_e_buf = d_rmark_e;
+  ctx->rmark_n_buf = d_rmark_n;
+  {
+    const char *fr = std::getenv("PDN_FULL_REPEAT");
+    ctx->full_repeat = fr != nullptr && fr[0] == '1' && fr[1] == '\0';
+  }
+  if (sweep_on) {
+    sweep.bnodes = P.bnodes;
+    sweep.n_bnodes = (int64_t)bnodes.size();
+    ctx->sweep = sweep;
+    ctx->Df.sweep = &ctx->sweep;
+  }
   // a^0 from the momentum equation at step 0 (Sec. 2.2.1): d^0 = 0 and no
   // contact at t^0, so the gravity acceleration on every free degree of
   // freedom; the first step then predicts d^1 and v^1 from it
@@ -893,32 +1023,33 @@ int pdn_set_impactor(pdn_ctx *ctx, double radius, double mass, const double cent
 int autotune(pdn_ctx *ctx) {
   if (ctx->tuned) return PDN_OK;
   ctx->tuned = true;
-  // variants timed by default: the hex kernel's four occupancy targets (the
-  // mixed hex + interface kernel, 4..7, is selected only by PDN_HEX_VARIANT:
-  // it times well in the first passes but loses once damage spreads)
+  // variants timed by default: the hex kernel's four occupancy targets with
+  // separate element and gather kernels, and the column sweep where it was
+  // planned (the mixed hex + interface kernel, 4..7, is selected only by
+  // PDN_HEX_VARIANT: it times well in the first passes but loses once damage
+  // spreads)
   const int nvar = ctx->precision == PDN_FP64 ? 1 : 4;
   const int nsel = ctx->precision == PDN_FP64 ? 1 : 8;
   if (nvar == 1) return PDN_OK;
-  // a fixed variant instead of timing (reproducible profiling runs)
+  const Sweep *sw = ctx->Df.sweep;
+  // a fixed variant instead of timing (reproducible profiling runs); the
+  // sweep stays as planned
   if (const char *fv = std::getenv("PDN_HEX_VARIANT")) {
     if (fv[0] >= '0' && fv[0] < '0' + nsel && fv[1] == '\0') {
       ctx->Df.hex_variant = fv[0] - '0';
       return PDN_OK;
     }
   }
-  cudaEvent_t ev[6];
-  for (int k = 0; k < 6; ++k) PDN_CU(cudaEventCreate(&ev[k]), "tune event");
-  int best = 0;
-  float best_ms = 1e30f;
+  cudaEvent_t ev[2];
+  for (int k = 0; k < 2; ++k) PDN_CU(cudaEventCreate(&ev[k]), "tune event");
   const int reps = 8;
-  for (int v = 0; v < nvar; ++v) {
-    ctx->Df.hex_variant = v;
+  // mean time of a whole internal-force pass as the graph runs it (the
+  // interface kernel on the forked stream where the variant uses one)
+  auto time_pass = [&](float &mean) -> int {
     float sum = 0.f;
     for (int r = 0; r <= reps; ++r) {
       int rc = set_mode(ctx, MODE_FORCES, ctx->ctl_host->step);
       if (rc) return rc;
-      // a whole internal-force pass as the graph runs it (the interface
-      // kernel on the forked stream where the variant uses one)
       PDN_CU(cudaEventRecord(ev[0], ctx->stream), "autotune record");
       cudaError_t e = run_pass(ctx, nullptr);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune pass");
@@ -928,14 +1059,36 @@ int autotune(pdn_ctx *ctx) {
       PDN_CU(cudaEventElapsedTime(&ms, ev[0], ev[1]), "autotune time");
       if (r > 0) sum += ms;  // the first pass warms up
     }
-    ctx->tune_ms[v] = sum / reps;
+    mean = sum / reps;
+    return PDN_OK;
+  };
+  int best = 0;
+  float best_ms = 1e30f;
+  ctx->Df.sweep = nullptr;
+  for (int v = 0; v < nvar; ++v) {
+    ctx->Df.hex_variant = v;
+    int rc = time_pass(ctx->tune_ms[v]);
+    if (rc) return rc;
     if (ctx->tune_ms[v] < best_ms) {
       best_ms = ctx->tune_ms[v];
       best = v;
     }
   }
   ctx->Df.hex_variant = best;
-  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  bool use_sweep = false;
+  if (sw) {
+    ctx->Df.sweep = sw;
+    int rc = time_pass(ctx->tune_ms[8]);
+    if (rc) return rc;
+    use_sweep = ctx->tune_ms[8] < best_ms;
+  }
+  ctx->Df.sweep = use_sweep ? sw : nullptr;
+  if (sw && !use_sweep && !ctx->full_repeat) {
+    // separate kernels: the local repetition of released steps again
+    ctx->Df.rmark_e = ctx->rmark_e_buf;
+    ctx->Df.rmark_n = ctx->rmark_n_buf;
+  }
+  for (int k = 0; k < 2; ++k) cudaEventDestroy(ev[k]);
   return PDN_OK;
 }
 
@@ -1231,7 +1384,7 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
   info->status = c.status;
   info->precision = ctx->precision;
   info->hex_variant = ctx->precision == PDN_FP64 ? ctx->Dd.hex_variant : ctx->Df.hex_variant;
-  info->reserved = 0;
+  info->sweep = (ctx->precision == PDN_FP32_FORCE && ctx->Df.sweep != nullptr) ? 1 + ctx->sweep.tile : 0;
   for (int v = 0; v < 12; ++v) info->tune_ms[v] = ctx->tune_ms[v];
   return PDN_OK;
 }

@@ -59,6 +59,9 @@ struct pdn_ctx {
   cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<cudaEvent_t> prof_ev;
   float *sur_buf = nullptr;  // learned-law parameters and scaling (pdn_set_surrogate)
+  pdn::Sweep sweep{};        // column sweep plan (Df.sweep points here when it is used)
+  uint8_t *rmark_e_buf = nullptr, *rmark_n_buf = nullptr;  // repetition marks (separate kernels)
+  bool full_repeat = false;  // PDN_FULL_REPEAT=1 at creation
   std::string err;
 
   // Pointers common to both precisions.

@@ -86,6 +86,32 @@ struct Mat {
   int32_t damage_on, plasticity_on;
 };
 
+// Column sweep of a layered plate (every hex and interface layer a full
+// nx x ny grid of columns, nodes numbered layer by layer, x fastest): one
+// launch evaluates the elements of a tile of columns layer by layer, bottom to
+// top, sums the forces of the nodes whose elements all lie in the tile in
+// shared memory (in the same order as the gather) and updates those nodes at
+// once; only the nodes on tile boundaries (and on the boundaries of the
+// z-chunks the sweep is split into) go through the element-force slots and a
+// gather over their list.
+constexpr int kMaxStages = 128;
+struct Sweep {
+  int32_t nx, ny;          // element columns
+  int32_t nxn;             // node columns along x (nx + 1)
+  int32_t n_stages;        // element layers, bottom to top
+  int64_t per_layer;       // nodes per node layer
+  int32_t tile;            // tile shape: 0 = 16 x 8, 1 = 8 x 8, 2 = 8 x 4 columns
+  int32_t tiles_x, tiles_y;
+  int32_t chunk_len;       // stages per z-chunk (the last may be shorter)
+  int32_t chunks;
+  int32_t pad;
+  const int32_t *bnodes;   // nodes updated by the gather over the list (ascending)
+  int64_t n_bnodes;
+  int32_t kind[kMaxStages];  // 0 hex layer, 1 interface layer
+  int32_t base[kMaxStages];  // first element id of the layer (hex or interface numbering)
+  int32_t bot[kMaxStages];   // bottom node layer; the top one is bot + 1
+};
+
 template <typename T>
 struct Vec4T;
 template <>
@@ -184,6 +210,10 @@ struct Dev {
   // range surf[s] = surf_base + s (then s and j convert without the index
   // arrays), else -1
   int32_t surf_base;
+  // column sweep of the pass (FP32 box hexes, flat interfaces, eight slots
+  // per node), or nullptr for separate element and gather kernels; a host
+  // pointer, read only by the launcher
+  const Sweep *sweep;
 };
 
 // Launchers (pdn_kernels.cu).

@@ -181,16 +181,22 @@ __host__ __device__ constexpr int pair_point(int p, int l) {
 // force sums run as packed pairs; the intralaminar law runs per point.
 // Same formulation as the scalar element below (Eq. fcont, Algorithm 4).
 // The compute of hex_item_box_pairs from the element's node displacements
-// ua (by node) and the x-y-z extents of the box (corner 6 minus corner 0).
+// ua (by node) and the x-y-z extents of the box (corner 6 minus corner 0);
+// the element's nodal forces f[8][3] are handed to store(f).
+template <typename Store>
 __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
                                                    const float (&ua)[8][3], float ex, float ey, float ez,
-                                                   bool pristine_in, int ply, const int4 *pos2, uint32_t rk);
+                                                   bool pristine_in, int ply, Store &&store);
 
-__device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode) {
+// Nodal forces of hex e (box, FP32) at the displacement mirror of the pass,
+// handed to store(f, nd) with the element's node ids; false when a repeated
+// pass does not evaluate it.
+template <typename Store>
+__device__ __forceinline__ bool hex_box_forces(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
+                                               Store &&store) {
   using V4 = float4;
   const Ctl *ctl = D.ctl;
-  if (e >= D.nh) return;
-  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, e)) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, e)) return false;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const V4 *PDN_STATE_RESTRICT U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
@@ -207,14 +213,27 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
   }
   const V4 x0 = D.X4[nd[0]], x6 = D.X4[nd[6]];
   const bool pristine_in = D.pflag[0] != nullptr && D.pflag[ctl->hpar][e] != 0;
-  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + e) : 0u;
   hex_box_pairs_core(D, M, e, mode, ua, x6.x - x0.x, x6.y - x0.y, x6.z - x0.z, pristine_in, D.ply[e],
-                     reinterpret_cast<const int4 *>(D.pos) + 2 * e, rk);
+                     [&](const float (&f)[8][3]) { store(f, nd); });
+  return true;
 }
 
+__device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode) {
+  if (e >= D.nh) return;
+  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + e) : 0u;
+  const int4 *pos2 = reinterpret_cast<const int4 *>(D.pos) + 2 * e;
+  hex_box_forces(D, M, e, mode, [&](const float (&f)[8][3], const int (&nd)[8]) {
+    int ps[8];
+    element_slots(D, D.hex, e, pos2, rk, ps);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
+  });
+}
+
+template <typename Store>
 __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Mat<float> &M, int64_t e, int mode,
                                                    const float (&ua)[8][3], float ex, float ey, float ez,
-                                                   bool pristine_in, int ply, const int4 *pos2, uint32_t rk) {
+                                                   bool pristine_in, int ply, Store &&store) {
   const Ctl *ctl = D.ctl;
   const int64_t nh = D.nh;
   const int hb = ctl->hpar;
@@ -416,10 +435,7 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
   float f[8][3];
   from_modes(C, f);
-  int ps[8];
-  element_slots(D, D.hex, e, pos2, rk, ps);
-#pragma unroll
-  for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
+  store(f);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,19 +660,20 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
 // FLAT: every interface is a flat axis-aligned rectangle (Dev::all_flat_coh):
 // the frame is the global axes and all four area weights are Lx Ly / 4, so
 // only two corners of the geometry are read and no root is taken.
-template <typename T, bool FLAT>
-__device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64_t c, int mode) {
+// Nodal forces of interface element c at the displacement mirror of the
+// pass, handed to store(f, nd) with the element's node ids; false when a
+// repeated pass does not evaluate it.
+template <typename T, bool FLAT, typename Store>
+__device__ __forceinline__ bool coh_forces(const Dev<T> &D, const Mat<T> &M, int64_t c, int mode, Store &&store) {
   using V4 = typename Vec4T<T>::type;
   const Ctl *ctl = D.ctl;
-  if (c >= D.nc) return;
-  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, D.nh + c)) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_e, D.nh + c)) return false;
   const int64_t nc = D.nc;
   const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
   const int hb = ctl->hpar;
   const V4 *PDN_STATE_RESTRICT U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
-  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + D.nh + c) : 0u;
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   constexpr int QX[4] = {-1, 1, 1, -1}, QY[4] = {-1, -1, 1, 1};
@@ -770,17 +787,28 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
     for (int p = 0; p < 4; ++p) rout[(int64_t)p * nc + c] = rv[p];
   }
   if (D.cflag[0] != nullptr) D.cflag[hb ^ 1][c] = still ? 1 : 0;
-  int ps[8];
-  element_slots(D, D.coh, c, reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c), rk, ps);
+  store(f, nd);
+  return true;
+}
+
+template <typename T, bool FLAT>
+__device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64_t c, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  if (c >= D.nc) return;
+  const uint32_t rk = D.rank != nullptr ? __ldg(D.rank + D.nh + c) : 0u;
+  coh_forces<T, FLAT>(D, M, c, mode, [&](const T (&f)[8][3], const int (&nd)[8]) {
+    int ps[8];
+    element_slots(D, D.coh, c, reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c), rk, ps);
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    V4 o;
-    o.x = f[a][0];
-    o.y = f[a][1];
-    o.z = f[a][2];
-    o.w = T(0);
-    D.fe[ps[a]] = o;
-  }
+    for (int a = 0; a < 8; ++a) {
+      V4 o;
+      o.x = f[a][0];
+      o.y = f[a][1];
+      o.z = f[a][2];
+      o.w = T(0);
+      D.fe[ps[a]] = o;
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -1138,64 +1166,50 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
 // inverse mass, d and v of the current buffer), then its element forces, up
 // to eight at once.  The forces are contiguous (written at their CSR
 // positions) and summed in CSR order: hexes, then interfaces, ascending.
+// State of node j that its update reads (flags, inverse mass, d and v of the
+// current buffer); issued before the element forces so that both rounds of
+// loads are in flight together.
 template <typename T>
-__device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
+struct NodeState {
+  uint8_t fl;
+  T im;
+  double dc[3], vc[3];
+};
+template <typename T>
+__device__ __forceinline__ void node_state_load(const Dev<T> &D, int64_t j, int mode, NodeState<T> &q) {
+  q.fl = 0;
+  q.im = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) q.dc[i] = q.vc[i] = 0.0;
+  if (mode == MODE_FORCES) return;
+  const int cur = D.ctl->dpar;
+  q.fl = D.nflag[j];
+  q.im = D.inv_mass[j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    q.dc[i] = D.d[cur][i * D.nn + j];
+    q.vc[i] = D.v[cur][i * D.nn + j];
+  }
+}
+
+// The update of node j from the sum (fx, fy, fz) of its element forces: the
+// internal-force output (MODE_FORCES), or the acceleration, the contact
+// reaction of an active node, and the predictor of the next step.
+template <typename T>
+__device__ __forceinline__ void node_update(const Dev<T> &D, int64_t j, int mode, const NodeState<T> &q, T fx,
+                                            T fy, T fz) {
   using V4 = typename Vec4T<T>::type;
-  if (j >= D.nn) return;
-  if (mode == MODE_REPEAT && !repeat_take(D.rmark_n, j)) return;
   Ctl *ctl = D.ctl;
   const int64_t nn = D.nn;
-  const bool stepping = mode != MODE_FORCES;
-  const bool ell = D.ell != 0;
-  const int r0 = ell ? 0 : D.row[j], r1 = ell ? 0 : D.row[j + 1];
-  int cur = 0;
-  uint8_t fl = 0;
-  T im = T(0);
-  double dc[3] = {0.0, 0.0, 0.0}, vc[3] = {0.0, 0.0, 0.0};
-  if (stepping) {
-    cur = ctl->dpar;
-    fl = D.nflag[j];
-    im = D.inv_mass[j];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      dc[i] = D.d[cur][i * nn + j];
-      vc[i] = D.v[cur][i * nn + j];
-    }
-  }
-  T fx = T(0), fy = T(0), fz = T(0);
-  if (ell) {
-    // the node's eight slots (CSR order, zero padding): one load round with
-    // the node state above
-    const V4 *fs = D.fe + 8 * j;
-    V4 f[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) f[k] = fs[k];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      fx += f[k].x;
-      fy += f[k].y;
-      fz += f[k].z;
-    }
-  }
-  for (int rb = r0; rb < r1; rb += 8) {
-    V4 f[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (rb + k < r1) f[k] = D.fe[rb + k];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (rb + k < r1) {
-        fx += f[k].x;
-        fy += f[k].y;
-        fz += f[k].z;
-      }
-  }
-  if (!stepping) {
+  if (mode == MODE_FORCES) {
     D.fout[j] = (double)fx;
     D.fout[nn + j] = (double)fy;
     D.fout[2 * nn + j] = (double)fz;
     return;
   }
+  const uint8_t fl = q.fl;
+  const T im = q.im;
+  const int cur = ctl->dpar;
   int nonfin = 0;
   const int nxt = cur ^ 1;
   double a[3];
@@ -1249,8 +1263,8 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const double ai = ((fl >> i) & 1) ? 0.0 : a[i];
-    const double v1 = vc[i] + dt * ai;
-    const double d1 = phi1 ? dc[i] + dt * v1 : dc[i] + dt * vc[i] + pdt2 * ai;
+    const double v1 = q.vc[i] + dt * ai;
+    const double d1 = phi1 ? q.dc[i] + dt * v1 : q.dc[i] + dt * q.vc[i] + pdt2 * ai;
     vn[i * nn + j] = v1;
     dn[i * nn + j] = d1;
     dd[i] = d1;
@@ -1262,6 +1276,46 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
   u.w = T(0);
   D.u4[nxt][j] = u;
   if (nonfin) atomicOr(&ctl->nonfinite, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  if (j >= D.nn) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_n, j)) return;
+  const bool ell = D.ell != 0;
+  const int r0 = ell ? 0 : D.row[j], r1 = ell ? 0 : D.row[j + 1];
+  NodeState<T> q;
+  node_state_load(D, j, mode, q);
+  T fx = T(0), fy = T(0), fz = T(0);
+  if (ell) {
+    // the node's eight slots (CSR order, zero padding): one load round with
+    // the node state above
+    const V4 *fs = D.fe + 8 * j;
+    V4 f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = fs[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      fx += f[k].x;
+      fy += f[k].y;
+      fz += f[k].z;
+    }
+  }
+  for (int rb = r0; rb < r1; rb += 8) {
+    V4 f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (rb + k < r1) f[k] = D.fe[rb + k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (rb + k < r1) {
+        fx += f[k].x;
+        fy += f[k].y;
+        fz += f[k].z;
+      }
+  }
+  node_update(D, j, mode, q, fx, fy, fz);
 }
 
 }  // namespace detail

@@ -111,6 +111,120 @@ __global__ void __launch_bounds__(256) k_tail(Dev<T> D) {
   tail_block<T, true>(D, mode);
 }
 
+// Column sweep (Sweep, pdn_internal.h): one block per tile of TX x TY
+// element columns and z-chunk, one thread per column.  Stage by stage (hex or
+// interface layer, bottom to top) each thread evaluates its column's element;
+// the force of every corner whose node column has all its elements in this
+// tile goes to a shared-memory slot (the node's rank, as in the gather), the
+// others to the global slots.  After a stage its bottom node layer is
+// complete: the nodes of the tile's complete columns sum their eight slots in
+// rank order, exactly as the gather does, take the same update (node_update)
+// and clear their slots for the layer two above.  Nodes on tile and chunk
+// boundaries are left to the gather over the list (k_gather_list).
+template <int TX, int TY>
+struct SweepSmem {
+  static constexpr int NC = (TX + 1) * (TY + 1);  // node columns of a tile
+  float s[2][8][3][NC];                            // [layer parity][rank][component][column]
+};
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D, Mat<float> M, Sweep S) {
+  constexpr int NT = TX * TY, NC = (TX + 1) * (TY + 1);
+  __shared__ SweepSmem<TX, TY> sm;
+  pdl_enter();
+  const int mode = D.ctl->mode;
+  if (mode >= MODE_DONE) return;
+  const int t = threadIdx.x;
+  const int tile = blockIdx.x % (S.tiles_x * S.tiles_y), chunk = blockIdx.x / (S.tiles_x * S.tiles_y);
+  const int i0 = (tile % S.tiles_x) * TX, j0 = (tile / S.tiles_x) * TY;
+  const int txe = min(TX, S.nx - i0), tye = min(TY, S.ny - j0);  // the tile's columns
+  const int k0 = chunk * S.chunk_len, k1 = min(S.n_stages, k0 + S.chunk_len);
+  // node column (ni, nj) of the tile: all its elements in the tile
+  auto complete = [&](int ni, int nj) {
+    return ni <= txe && nj <= tye && (ni > 0 || i0 == 0) && (ni < txe || i0 + txe == S.nx) &&
+           (nj > 0 || j0 == 0) && (nj < tye || j0 + tye == S.ny);
+  };
+  // a node layer is summed here unless it is shared with the chunk below/above
+  auto layer_here = [&](int L) { return (L > S.bot[k0] || k0 == 0) && (L < S.bot[k1 - 1] + 1 || k1 == S.n_stages); };
+  for (int q = t; q < 2 * 8 * 3 * NC; q += NT) (&sm.s[0][0][0][0])[q] = 0.0f;
+  const int ti = t % TX, tj = t / TX;
+  const bool col = ti < txe && tj < tye;
+  const int gi = i0 + ti, gj = j0 + tj;
+  // corners 0..3: (0,0), (1,0), (1,1), (0,1) of the column's quad; 4..7 above
+  const int cdx[4] = {0, 1, 1, 0}, cdy[4] = {0, 0, 1, 1};
+  bool cmask[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) cmask[a] = complete(ti + cdx[a], tj + cdy[a]);
+  __syncthreads();
+
+  auto gather_layer = [&](int L) {
+    const int p = L & 1;
+    for (int q = t; q < NC; q += NT) {
+      const int ni = q % (TX + 1), nj = q / (TX + 1);
+      if (!complete(ni, nj)) continue;
+      const int64_t j = (int64_t)L * S.per_layer + (int64_t)(j0 + nj) * S.nxn + (i0 + ni);
+      NodeState<float> st;
+      node_state_load(D, j, mode, st);
+      float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        fx += sm.s[p][r][0][q];
+        fy += sm.s[p][r][1][q];
+        fz += sm.s[p][r][2][q];
+        sm.s[p][r][0][q] = 0.0f;
+        sm.s[p][r][1][q] = 0.0f;
+        sm.s[p][r][2][q] = 0.0f;
+      }
+      node_update(D, j, mode, st, fx, fy, fz);
+    }
+  };
+
+  for (int k = k0; k < k1; ++k) {
+    const int L = S.bot[k];
+    const bool lo_here = layer_here(L), hi_here = layer_here(L + 1);
+    if (col) {
+      const int64_t el = (int64_t)S.base[k] + (int64_t)gj * S.nx + gi;
+      auto store = [&](const float (&f)[8][3], const int (&nd)[8]) {
+        const uint32_t rk = __ldg(D.rank + (S.kind[k] ? D.nh + el : el));
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const int r = (int)((rk >> (3 * a)) & 7u);
+          const int c = a & 3;
+          const bool here = cmask[c] && (a < 4 ? lo_here : hi_here);
+          if (here) {
+            const int q = (tj + cdy[c]) * (TX + 1) + ti + cdx[c];
+            const int p = (a < 4 ? L : L + 1) & 1;
+            sm.s[p][r][0][q] = f[a][0];
+            sm.s[p][r][1][q] = f[a][1];
+            sm.s[p][r][2][q] = f[a][2];
+          } else {
+            D.fe[8 * (int64_t)nd[a] + r] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
+          }
+        }
+      };
+      if (S.kind[k] == 0)
+        hex_box_forces(D, M, el, mode, store);
+      else
+        coh_forces<float, true>(D, M, el, mode, store);
+    }
+    __syncthreads();
+    if (lo_here) gather_layer(L);
+    __syncthreads();
+  }
+  const int Ltop = S.bot[k1 - 1] + 1;
+  if (layer_here(Ltop)) gather_layer(Ltop);
+}
+
+// The gather over a list of nodes (the sweep's boundary nodes).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_list(Dev<T> D, const int32_t *list, int64_t n) {
+  pdl_enter();
+  const int mode = D.ctl->mode;
+  if (mode >= MODE_DONE) return;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) gather_item(D, (int64_t)list[q], mode);
+}
+
 // After pdn_set_impactor: the striker of the first step to be computed.
 __global__ void k_striker_init(Striker *S, StrikerStep *ss, double dt) {
   double c1[3], w1[3], aI[3];
@@ -302,9 +416,38 @@ void launch_coh(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, bool pdl) {
 // side stream with fork/join events is given: the interface kernel runs on the
 // side stream), then the gather and the tail.  With ev
 // (profiling) the kernels run one after another with an event between each.
+// The sweep's element-and-node launch for its tile shape.
+inline void launch_sweep(const Dev<float> &D, const Mat<float> &M, cudaStream_t s) {
+  const Sweep &S = *D.sweep;
+  const int g = S.tiles_x * S.tiles_y * S.chunks;
+  switch (S.tile) {
+    case 0: launch_k(k_sweep<16, 8>, g, 128, s, D, M, S); break;
+    case 1: launch_k(k_sweep<8, 8>, g, 64, s, D, M, S); break;
+    default: launch_k(k_sweep<8, 4>, g, 32, s, D, M, S); break;
+  }
+}
+
 template <typename T>
 cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_t gather_block,
                         cudaEvent_t *ev, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (D.sweep != nullptr && D.sur_params == nullptr) {
+      // contact, the sweep (elements and most nodes), the gather over the
+      // boundary nodes, the tail; the interface event pair is empty
+      if (ev) cudaEventRecord(ev[0], s);
+      launch_k(k_contact<T>, grid_of(D.ns, kActRun), kActRun, s, D);
+      if (ev) cudaEventRecord(ev[1], s);
+      launch_sweep(D, M, s);
+      if (ev) cudaEventRecord(ev[2], s);
+      if (ev) cudaEventRecord(ev[3], s);
+      if (D.sweep->n_bnodes > 0)
+        launch_k(k_gather_list<T>, grid_of(D.sweep->n_bnodes, 256), 256, s, D, D.sweep->bnodes, D.sweep->n_bnodes);
+      if (ev) cudaEventRecord(ev[4], s);
+      launch_k(k_tail<T>, 1, 256, s, D);
+      if (ev) cudaEventRecord(ev[5], s);
+      return cudaGetLastError();
+    }
+  }
   bool mixed = D.hex_variant >= kMixedVariant;
   if constexpr (std::is_same<T, float>::value) mixed = mixed && D.sur_params == nullptr;
   if (mixed) {
