@@ -177,7 +177,8 @@ typedef struct {
                               mesh allows it and kept by the autotuner of the first
                               pdn_step when it is faster.  The environment variable
                               PDN_SWEEP=0, read by pdn_init_mesh, keeps the separate
-                              kernels */
+                              kernels; PDN_SWEEP=1, read by the first pdn_step, keeps
+                              the sweep whatever the timing */
   double tune_ms[12];      /* mean time of an internal-force pass with each variant when
                               tuned (0 if not): entries 0..3 the hex variants with separate
                               kernels, entry 8 the column sweep (0 where none was planned);

@@ -336,13 +336,15 @@ bool plan_sweep(int64_t nn, int64_t nh, int64_t nc, const int32_t *hex, const in
     S.base[L] = base[k];
     S.bot[L] = bot[k];
   }
-  // tile shape and z-chunks: at least eight blocks per SM in total
+  // tile shape: the largest whose tiles alone give every SM at least eight
+  // blocks; z-chunks: enough blocks for about eight rounds of the resident
+  // blocks (4, 8 or 16 per SM for the three shapes at 128 registers), so that
+  // the last, partial round is a small part of the launch
   static const int TXS[3] = {16, 8, 8}, TYS[3] = {8, 8, 4};
-  const int64_t want = (int64_t)8 * n_sm;
   int t = 2;
   for (int c = 0; c < 3; ++c) {
     const int64_t tiles = ((nx + TXS[c] - 1) / TXS[c]) * ((ny + TYS[c] - 1) / TYS[c]);
-    if (tiles >= want) {
+    if (tiles >= (int64_t)8 * n_sm) {
       t = c;
       break;
     }
@@ -351,8 +353,10 @@ bool plan_sweep(int64_t nn, int64_t nh, int64_t nc, const int32_t *hex, const in
   S.tiles_x = (int32_t)((nx + TXS[t] - 1) / TXS[t]);
   S.tiles_y = (int32_t)((ny + TYS[t] - 1) / TYS[t]);
   const int64_t tiles = (int64_t)S.tiles_x * S.tiles_y;
+  const int64_t resident = (int64_t)n_sm * (512 / (TXS[t] * TYS[t]));
+  const int64_t want = 8 * resident;
   int64_t chunks = std::max<int64_t>(1, (want + tiles - 1) / tiles);
-  chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, n_st / 4));  // at least four stages per chunk
+  chunks = std::min<int64_t>(chunks, std::max<int64_t>(1, n_st / 8));  // at least eight stages per chunk
   S.chunk_len = (int32_t)((n_st + chunks - 1) / chunks);
   S.chunks = (int32_t)((n_st + S.chunk_len - 1) / S.chunk_len);
   // boundary nodes: tile-boundary columns of every node layer, and every
@@ -1080,7 +1084,9 @@ int autotune(pdn_ctx *ctx) {
     ctx->Df.sweep = sw;
     int rc = time_pass(ctx->tune_ms[8]);
     if (rc) return rc;
-    use_sweep = ctx->tune_ms[8] < best_ms;
+    // PDN_SWEEP=1 keeps the sweep whatever the timing
+    const char *sv = std::getenv("PDN_SWEEP");
+    use_sweep = ctx->tune_ms[8] < best_ms || (sv && sv[0] == '1' && sv[1] == '\0');
   }
   ctx->Df.sweep = use_sweep ? sw : nullptr;
   if (sw && !use_sweep && !ctx->full_repeat) {

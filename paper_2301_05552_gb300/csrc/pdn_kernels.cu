@@ -125,7 +125,19 @@ template <int TX, int TY>
 struct SweepSmem {
   static constexpr int NC = (TX + 1) * (TY + 1);  // node columns of a tile
   float s[2][8][3][NC];                            // [layer parity][rank][component][column]
+  double dv[6][NC];                                // d and v of the layer to update, copied ahead
 };
+
+// 8-byte asynchronous copy global -> shared (cp.async; completed by
+// cp_async_wait_all in the issuing thread).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
 
 template <int TX, int TY>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D, Mat<float> M, Sweep S) {
@@ -157,6 +169,22 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
   for (int a = 0; a < 4; ++a) cmask[a] = complete(ti + cdx[a], tj + cdy[a]);
   __syncthreads();
 
+  // the displacement and velocity of the nodes a gather of layer L updates,
+  // copied into shared memory while the stage's elements are computed
+  const int cur = D.ctl->dpar;
+  auto prefetch_layer = [&](int L) {
+    if (mode == MODE_FORCES) return;
+    for (int q = t; q < NC; q += NT) {
+      const int ni = q % (TX + 1), nj = q / (TX + 1);
+      if (!complete(ni, nj)) continue;
+      const int64_t j = (int64_t)L * S.per_layer + (int64_t)(j0 + nj) * S.nxn + (i0 + ni);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        cp_async8(&sm.dv[i][q], D.d[cur] + i * D.nn + j);
+        cp_async8(&sm.dv[3 + i][q], D.v[cur] + i * D.nn + j);
+      }
+    }
+  };
   auto gather_layer = [&](int L) {
     const int p = L & 1;
     for (int q = t; q < NC; q += NT) {
@@ -164,7 +192,19 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
       if (!complete(ni, nj)) continue;
       const int64_t j = (int64_t)L * S.per_layer + (int64_t)(j0 + nj) * S.nxn + (i0 + ni);
       NodeState<float> st;
-      node_state_load(D, j, mode, st);
+      st.fl = 0;
+      st.im = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) st.dc[i] = st.vc[i] = 0.0;
+      if (mode != MODE_FORCES) {
+        st.fl = D.nflag[j];
+        st.im = D.inv_mass[j];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          st.dc[i] = sm.dv[i][q];
+          st.vc[i] = sm.dv[3 + i][q];
+        }
+      }
       float fx = 0.0f, fy = 0.0f, fz = 0.0f;
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
@@ -182,6 +222,7 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
   for (int k = k0; k < k1; ++k) {
     const int L = S.bot[k];
     const bool lo_here = layer_here(L), hi_here = layer_here(L + 1);
+    if (lo_here) prefetch_layer(L);
     if (col) {
       const int64_t el = (int64_t)S.base[k] + (int64_t)gj * S.nx + gi;
       auto store = [&](const float (&f)[8][3], const int (&nd)[8]) {
@@ -207,12 +248,18 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
       else
         coh_forces<float, true>(D, M, el, mode, store);
     }
+    cp_async_wait_all();
     __syncthreads();
     if (lo_here) gather_layer(L);
     __syncthreads();
   }
   const int Ltop = S.bot[k1 - 1] + 1;
-  if (layer_here(Ltop)) gather_layer(Ltop);
+  if (layer_here(Ltop)) {
+    prefetch_layer(Ltop);
+    cp_async_wait_all();
+    __syncthreads();
+    gather_layer(Ltop);
+  }
 }
 
 // The gather over a list of nodes (the sweep's boundary nodes).

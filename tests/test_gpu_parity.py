@@ -246,7 +246,11 @@ def test_release_and_repeat_matches_oracle(pkg):
     assert g.state()[2]["velocity"][2] == pytest.approx(o.impactor()["velocity"][2], rel=1e-9)
 
 
-def test_deterministic(pkg):
+def test_deterministic(pkg, monkeypatch):
+    """Two runs of the same launch configuration give bitwise the same state
+    (the element-kernel variant is fixed: the autotuner may pick variants
+    that contract multiply-adds differently)."""
+    monkeypatch.setenv("PDN_HEX_VARIANT", "0")
     w = _damage_plate(fp64=False)
     st = _damaging_state(w)
     out = []

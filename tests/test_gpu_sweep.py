@@ -119,9 +119,9 @@ def test_sweep_against_oracle_through_release(pkg, monkeypatch):
 
 
 def test_full_size_plates_plan_a_sweep(pkg):
-    """The 128x192x16 plate gets 8 x 4 tiles in two z-chunks, the 400x600x32
-    plate 16 x 8 tiles in one chunk (the tile and chunk choice fills 152 SMs
-    with eight blocks each)."""
+    """The 128x192x16 plate gets 8 x 4 tiles, the 400x600x32 plate 16 x 8
+    tiles (the first shape whose tiles give each of the 152 SMs eight
+    blocks)."""
     for w, tile in ((pi.damage_fp32_plate(), 3), (pi.large_fp32_plate(), 1)):
         c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP32_FORCE)
         info = pkg.pdn_get_info(c)
