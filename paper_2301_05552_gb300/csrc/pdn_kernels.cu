@@ -126,7 +126,16 @@ struct SweepSmem {
   static constexpr int NC = (TX + 1) * (TY + 1);  // node columns of a tile
   float s[2][8][3][NC];                            // [layer parity][rank][component][column]
   double dv[6][NC];                                // d and v of the layer to update, copied ahead
+  uint32_t flw[NC];                                // the 4-byte word holding each node's flag byte
+  float im[NC];                                    // inverse lumped mass
 };
+
+// 4-byte asynchronous copy global -> shared.
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
 
 // 8-byte asynchronous copy global -> shared (cp.async; completed by
 // cp_async_wait_all in the issuing thread).
@@ -183,6 +192,9 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
         cp_async8(&sm.dv[i][q], D.d[cur] + i * D.nn + j);
         cp_async8(&sm.dv[3 + i][q], D.v[cur] + i * D.nn + j);
       }
+      // the flag array is padded to whole 4-byte words
+      cp_async4(&sm.flw[q], D.nflag + (j & ~int64_t(3)));
+      cp_async4(&sm.im[q], D.inv_mass + j);
     }
   };
   auto gather_layer = [&](int L) {
@@ -197,8 +209,8 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
 #pragma unroll
       for (int i = 0; i < 3; ++i) st.dc[i] = st.vc[i] = 0.0;
       if (mode != MODE_FORCES) {
-        st.fl = D.nflag[j];
-        st.im = D.inv_mass[j];
+        st.fl = (uint8_t)(sm.flw[q] >> (8 * (int)(j & 3)));
+        st.im = sm.im[q];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
           st.dc[i] = sm.dv[i][q];
