@@ -1037,11 +1037,25 @@ int autotune(pdn_ctx *ctx) {
   const int nsel = ctx->precision == PDN_FP64 ? 1 : 8;
   if (nvar == 1) return PDN_OK;
   const Sweep *sw = ctx->Df.sweep;
-  // a fixed variant instead of timing (reproducible profiling runs); the
-  // sweep stays as planned
+  // the sweep is kept only on request (PDN_SWEEP=1): the internal-force pass
+  // the autotuner times does not show the cost of the node update in a
+  // stepping pass, which the sweep carries inside its element launch; there
+  // it measured slower (400x600x32 plate: 1.59 against 1.29 ms per step)
+  const char *sv = std::getenv("PDN_SWEEP");
+  const bool keep_sweep = sw && sv && sv[0] == '1' && sv[1] == '\0';
+  auto drop_sweep = [&] {
+    ctx->Df.sweep = nullptr;
+    if (!ctx->full_repeat) {
+      // separate kernels: the local repetition of released steps again
+      ctx->Df.rmark_e = ctx->rmark_e_buf;
+      ctx->Df.rmark_n = ctx->rmark_n_buf;
+    }
+  };
+  // a fixed variant instead of timing (reproducible profiling runs)
   if (const char *fv = std::getenv("PDN_HEX_VARIANT")) {
     if (fv[0] >= '0' && fv[0] < '0' + nsel && fv[1] == '\0') {
       ctx->Df.hex_variant = fv[0] - '0';
+      if (sw && !keep_sweep) drop_sweep();
       return PDN_OK;
     }
   }
@@ -1080,23 +1094,11 @@ int autotune(pdn_ctx *ctx) {
     }
   }
   ctx->Df.hex_variant = best;
-  bool use_sweep = false;
   if (sw) {
     ctx->Df.sweep = sw;
     int rc = time_pass(ctx->tune_ms[8]);
     if (rc) return rc;
-    // the internal-force pass does not show the cost of the node update in
-    // a stepping pass, which the sweep carries inside its element launch;
-    // there it measured slower (400x600x32 plate: 1.59 against 1.29 ms per
-    // step), so it is kept only on request: PDN_SWEEP=1
-    const char *sv = std::getenv("PDN_SWEEP");
-    use_sweep = sv && sv[0] == '1' && sv[1] == '\0';
-  }
-  ctx->Df.sweep = use_sweep ? sw : nullptr;
-  if (sw && !use_sweep && !ctx->full_repeat) {
-    // separate kernels: the local repetition of released steps again
-    ctx->Df.rmark_e = ctx->rmark_e_buf;
-    ctx->Df.rmark_n = ctx->rmark_n_buf;
+    if (!keep_sweep) drop_sweep();
   }
   for (int k = 0; k < 2; ++k) cudaEventDestroy(ev[k]);
   return PDN_OK;

@@ -27,14 +27,11 @@ def pkg():
 
 
 def _solver(pkg, w, sweep, monkeypatch):
+    """A solver with the sweep (PDN_SWEEP=1, read at creation and by the first
+    step) or without it (PDN_SWEEP=0), element variant 0 on both sides."""
     monkeypatch.setenv("PDN_HEX_VARIANT", "0")
-    if sweep:
-        monkeypatch.delenv("PDN_SWEEP", raising=False)
-    else:
-        monkeypatch.setenv("PDN_SWEEP", "0")
-    s = pkg.Solver(w)
-    monkeypatch.delenv("PDN_SWEEP", raising=False)
-    return s
+    monkeypatch.setenv("PDN_SWEEP", "1" if sweep else "0")
+    return pkg.Solver(w)
 
 
 def _plates():
@@ -65,8 +62,11 @@ def test_sweep_equals_separate_kernels(pkg, monkeypatch, name, w, seeded):
         st = pi.seeded_state(w.plate, 7, amp=0.02, vamp=300.0, dimple=(0.5 * Lx, 0.5 * Ly, 0.12, 1.5))
         pkg.pdn_set_state(a.ctx, *st)
         pkg.pdn_set_state(b.ctx, *st)
+    monkeypatch.setenv("PDN_SWEEP", "1")
     a.step(w.steps)
+    monkeypatch.setenv("PDN_SWEEP", "0")
     b.step(w.steps)
+    assert pkg.pdn_get_info(a.ctx)["sweep"] > 0 and pkg.pdn_get_info(b.ctx)["sweep"] == 0
     da, va, _ = a.state()
     db, vb, _ = b.state()
     fa, fb = a.force_history(), b.force_history()
