@@ -743,7 +743,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       P.pflag[b] = A.take<uint8_t>((nh + 15) & ~int64_t(15));
       P.cflag[b] = A.take<uint8_t>(nc1);
     }
-    P.fe = A.take<char>(ts * 3 * n_slots);
+    P.fe = A.take<char>(ts * 4 * n_slots);
     P.rel = A.take<uint8_t>(ns1);
     P.act_cnt = A.take<int32_t>(sizeof(int32_t) * ((ns1 + kActRun - 1) / kActRun));
     P.rmark_e = A.take<uint8_t>(nh + nc);
@@ -862,7 +862,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       k_fill_hist_float<<<grid_of(nh * 8 * 7, 256), 256>>>(reinterpret_cast<float *>(d_hist[b]), nh * 8, 4);
     chk(cudaGetLastError());
   }
-  chk(cudaMemset(d_fe, 0, ts * 3 * n_slots));  // the padding slots stay zero
+  chk(cudaMemset(d_fe, 0, ts * 4 * n_slots));  // the padding slots stay zero
   chk(cudaMemset(d_rel, 0, std::max<int64_t>(ns, 1)));
   chk(cudaMemset(d_rmark_e, 0, nh + nc));
   chk(cudaMemset(d_rmark_n, 0, nn));
@@ -918,7 +918,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       D.pflag[b] = P.pflag[b];
       D.cflag[b] = P.cflag[b];
     }
-    D.fe = reinterpret_cast<T *>(d_fe);
+    D.fe = reinterpret_cast<V4 *>(d_fe);
     D.rel = d_rel;
     D.act_cnt = P.act_cnt;
     // PDN_FULL_REPEAT=1: repeated passes evaluate every element and node

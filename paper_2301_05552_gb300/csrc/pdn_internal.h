@@ -157,7 +157,7 @@ struct Dev {
   // always read and written).
   uint8_t *pflag[2];       // [nh]
   uint8_t *cflag[2];       // [nc]
-  T *fe;                   // element nodal forces, three components per slot: slot s at fe[3 s]
+  V4 *fe;                  // [(nh + nc) * 8] element nodal forces
   // contact
   uint8_t *act[2];         // [ns] contact set by step parity
   uint8_t *rel;            // [ns] released in the current step

@@ -30,16 +30,6 @@ namespace pdn {
 namespace detail {
 
 // ---------------------------------------------------------------------------
-// An element-force slot holds the three components of one element's force on
-// one node (12 bytes in FP32): slot s at fe[3 s].
-template <typename T>
-__device__ __forceinline__ void slot_store(T *fe, int64_t s, T fx, T fy, T fz) {
-  T *p = fe + 3 * s;
-  p[0] = fx;
-  p[1] = fy;
-  p[2] = fz;
-}
-
 // Slots of an element's eight nodal forces.  With eight slots per node
 // (D.rank set) slot = 8 node + rank, the node ids re-read from the
 // connectivity (still in L1 from the element's start) and the ranks packed
@@ -236,7 +226,7 @@ __device__ __forceinline__ void hex_item_box_pairs(const Dev<float> &D, const Ma
     int ps[8];
     element_slots(D, D.hex, e, pos2, rk, ps);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) slot_store(D.fe, ps[a], f[a][0], f[a][1], f[a][2]);
+    for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
   });
 }
 
@@ -654,7 +644,14 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
   const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * e + 1);
   const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-  for (int a = 0; a < 8; ++a) slot_store(D.fe, ps[a], f[a][0], f[a][1], f[a][2]);
+  for (int a = 0; a < 8; ++a) {
+    V4 o;
+    o.x = f[a][0];
+    o.y = f[a][1];
+    o.z = f[a][2];
+    o.w = T(0);
+    D.fe[ps[a]] = o;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -803,7 +800,14 @@ __device__ __forceinline__ void coh_item(const Dev<T> &D, const Mat<T> &M, int64
     int ps[8];
     element_slots(D, D.coh, c, reinterpret_cast<const int4 *>(D.pos) + 2 * (D.nh + c), rk, ps);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) slot_store(D.fe, ps[a], f[a][0], f[a][1], f[a][2]);
+    for (int a = 0; a < 8; ++a) {
+      V4 o;
+      o.x = f[a][0];
+      o.y = f[a][1];
+      o.z = f[a][2];
+      o.w = T(0);
+      D.fe[ps[a]] = o;
+    }
   });
 }
 
@@ -1285,42 +1289,30 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
   node_state_load(D, j, mode, q);
   T fx = T(0), fy = T(0), fz = T(0);
   if (ell) {
-    // the node's eight slots (CSR order, zero padding), 24 contiguous values
-    // loaded as 16-byte vectors: one load round with the node state above
-    using L16 = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
-    constexpr int kPer = 16 / sizeof(T), kVec = 24 / kPer;
-    const L16 *fs = reinterpret_cast<const L16 *>(D.fe + 24 * j);
-    T f[24];
+    // the node's eight slots (CSR order, zero padding): one load round with
+    // the node state above
+    const V4 *fs = D.fe + 8 * j;
+    V4 f[8];
 #pragma unroll
-    for (int k = 0; k < kVec; ++k) {
-      const L16 q4 = fs[k];
-      const T *qq = reinterpret_cast<const T *>(&q4);
-#pragma unroll
-      for (int c = 0; c < kPer; ++c) f[k * kPer + c] = qq[c];
-    }
+    for (int k = 0; k < 8; ++k) f[k] = fs[k];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      fx += f[3 * k];
-      fy += f[3 * k + 1];
-      fz += f[3 * k + 2];
+      fx += f[k].x;
+      fy += f[k].y;
+      fz += f[k].z;
     }
   }
   for (int rb = r0; rb < r1; rb += 8) {
-    T f[8][3];
+    V4 f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (rb + k < r1) f[k] = D.fe[rb + k];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if (rb + k < r1) {
-        const T *p = D.fe + 3 * (int64_t)(rb + k);
-        f[k][0] = p[0];
-        f[k][1] = p[1];
-        f[k][2] = p[2];
-      }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (rb + k < r1) {
-        fx += f[k][0];
-        fy += f[k][1];
-        fz += f[k][2];
+        fx += f[k].x;
+        fy += f[k].y;
+        fz += f[k].z;
       }
   }
   node_update(D, j, mode, q, fx, fy, fz);

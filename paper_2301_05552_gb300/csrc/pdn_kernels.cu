@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY)) k_sweep(Dev<float> D
             sm.s[p][r][1][q] = f[a][1];
             sm.s[p][r][2][q] = f[a][2];
           } else {
-            slot_store(D.fe, 8 * (int64_t)nd[a] + r, f[a][0], f[a][1], f[a][2]);
+            D.fe[8 * (int64_t)nd[a] + r] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
           }
         }
       };

@@ -118,7 +118,7 @@ cudaError_t run_noalloc(unsigned char *base, int64_t nn, int64_t nh, const int32
   T *hin = history ? const_cast<T *>(reinterpret_cast<const T *>(history)) : reinterpret_cast<T *>(base + kOffHin);
   D.hist[0] = hin;
   D.hist[1] = reinterpret_cast<T *>(base + kOffHout);
-  D.fe = reinterpret_cast<T *>(base + kOffFe);
+  D.fe = reinterpret_cast<V4 *>(base + kOffFe);
   D.ctl = reinterpret_cast<Ctl *>(base);
   D.fout = f_int;
   const int64_t work = std::max<int64_t>(nn, 1);

@@ -640,12 +640,7 @@ __global__ void __launch_bounds__(kHexSurBlock, 3) k_hex_sur(Dev<float> D, Mat<f
   const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * el + 1);
   const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    float *q = D.fe + 3 * (int64_t)ps[a];
-    q[0] = f[a][0];
-    q[1] = f[a][1];
-    q[2] = f[a][2];
-  }
+  for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
 }
 
 thread_local std::string g_sur_error;
