@@ -4,8 +4,12 @@
  * parameters) maps the elastic strain of a Gauss point (ply axes, engineering
  * shear, after the exact shear plasticity of Algorithm 4) and its four damage
  * thresholds r_FT, r_FC, r_MT, r_MC to the nominal stress and the updated
- * thresholds.  Weights are BF16 with FP32 accumulation on the tensor cores
- * (mma.sync m16n8k16); training keeps FP32 master weights (Adam).
+ * thresholds.  Weights are BF16 with FP32 accumulation on the Blackwell
+ * tensor cores (tcgen05.mma with the accumulators in tensor memory, 128
+ * points per CTA) in training (forward, backward, weight gradients) and in
+ * inference; training keeps FP32 master weights (Adam).  Every wait on the
+ * tensor core is bounded: one that gives up returns PDN_E_TIMEOUT from the
+ * call (or halts a stepping context with it).
  *
  * Training data come from the library's own exact law on the GPU (the same
  * device code the hex kernel runs, checked against the FP64 CPU law in the

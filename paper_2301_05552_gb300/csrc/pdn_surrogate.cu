@@ -1,9 +1,8 @@
 // Learned surrogate of the intralaminar damage law (include/pdn_surrogate.h):
 // training data from the exact law on the GPU, training (forward, backward,
-// weight gradients, Adam; warp-level mma.sync m16n8k16 tiles of 16 points)
-// and inference on the Blackwell tensor cores (tcgen05.mma with TMEM
-// accumulators, 128 points per CTA), BF16 operands and FP32 accumulation, and
-// the hook that lets the hex kernel use it.
+// weight gradients, Adam) and inference on the Blackwell tensor cores
+// (tcgen05.mma with TMEM accumulators, 128 points per CTA), BF16 operands and
+// FP32 accumulation, and the hook that lets the hex kernel use it.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,7 +31,6 @@ namespace {
 using namespace detail;
 using namespace mlp;
 
-constexpr int kWarps = 4;                 // warps per block of the tile kernels
 constexpr int kChunk = 128;               // points per weight-gradient partial
 constexpr int kLayers = 4;
 // padded output and input widths of layer l (0..3)
@@ -115,77 +113,6 @@ __global__ void k_law_points(LawArgs A, const float *in, float *out, int64_t n) 
 }
 
 // ---------------------------------------------------------------------------
-// Tile kernels.  Shared memory of a block: the network, then per warp its
-// tiles.
-
-struct WarpTiles {
-  __nv_bfloat16 a0[16 * kS16];      // normalised inputs
-  __nv_bfloat16 a[3][16 * kS64];    // hidden activations (relu), bf16
-  __nv_bfloat16 g16[16 * kS16];     // output-layer gradient, bf16
-  __nv_bfloat16 g64[16 * kS64];     // hidden-layer gradient, bf16
-  float y[16 * kOutPad];            // normalised outputs
-};
-
-__device__ __forceinline__ WarpTiles &warp_tiles(unsigned char *smem) {
-  return reinterpret_cast<WarpTiles *>(smem + sizeof(SmemNet))[threadIdx.x >> 5];
-}
-
-// Normalised bf16 input tile from raw rows (row index of tile row r: idx(r)).
-template <typename IdxF>
-__device__ __forceinline__ void load_inputs(__nv_bfloat16 *a0, const float *X, const Scaling &sc, IdxF idx) {
-  const int l = threadIdx.x & 31;
-  for (int e = l; e < 16 * kInPad; e += 32) {
-    const int r = e / kInPad, c = e % kInPad;
-    float v = 0.0f;
-    if (c < kIn) {
-      const int64_t row = idx(r);
-      v = (X[row * kIn + c] - sc.in_shift[c]) * sc.in_mul[c];
-    }
-    a0[r * kS16 + c] = __float2bfloat16_rn(v);
-  }
-}
-
-// acc[NT][4] = G[16][16*KT] W with W [16*KT][8*NT] stored as W [n][k] row-major
-// (the backward product through a layer: rows of W are the layer's outputs).
-template <int KT, int NT>
-__device__ __forceinline__ void layer_back(const __nv_bfloat16 *G, int gs, const __nv_bfloat16 *W, int ws,
-                                           float (&acc)[NT][4]) {
-  const int l = threadIdx.x & 31;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.0f;
-#pragma unroll
-  for (int kt = 0; kt < KT; ++kt) {
-    uint32_t a[4];
-    ldsm_x4(a, a_ptr(G, gs, kt * 16));
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      uint32_t b[2];
-      ldsm_x2_t(b, W + (kt * 16 + (l & 15)) * ws + nt * 8);
-      mma16816(acc[nt], a, b);
-    }
-  }
-}
-
-// dZ = acc * relu'(z) (the mask is a > 0 of the stored bf16 activation),
-// as fp32 to global rows and as bf16 into the gradient tile.
-template <int NT>
-__device__ __forceinline__ void store_grad(const float (&acc)[NT][4], const __nv_bfloat16 *act, float *dz_out,
-                                           __nv_bfloat16 *g, int gs) {
-  const int l = threadIdx.x & 31, gr = l >> 2, t = l & 3;
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      const int r = gr + 8 * hf, c = nt * 8 + 2 * t;
-      const float m0 = __bfloat162float(act[r * kS64 + c]) > 0.0f ? 1.0f : 0.0f;
-      const float m1 = __bfloat162float(act[r * kS64 + c + 1]) > 0.0f ? 1.0f : 0.0f;
-      const float v0 = acc[nt][2 * hf] * m0, v1 = acc[nt][2 * hf + 1] * m1;
-      dz_out[r * kHid + c] = v0;
-      dz_out[r * kHid + c + 1] = v1;
-      *reinterpret_cast<__nv_bfloat162 *>(g + r * gs + c) = __floats2bfloat162_rn(v0, v1);
-    }
-}
-
 struct TrainBufs {
   __nv_bfloat16 *A0;      // [B][16]
   __nv_bfloat16 *A[3];    // [B][64]
@@ -194,148 +121,181 @@ struct TrainBufs {
   float *loss_part;       // [B / 16] per tile
 };
 
-// Forward and backward through the activations for B points (one tile of 16
-// per warp): rows idx(i) of X (raw inputs) and T (raw targets), scaled by sc.
-// Loss = mean over points and the kOut outputs of (y_n - t_n)^2.
-__global__ void __launch_bounds__(kWarps * 32) k_train_tiles(const float *params, Scaling sc, const float *X,
-                                                             const float *T, int64_t n_rows, int64_t B,
-                                                             int32_t random, uint64_t seed, TrainBufs tb) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  SmemNet &N = *reinterpret_cast<SmemNet *>(smem);
-  load_net(N, params);
-  __syncthreads();
-  WarpTiles &W = warp_tiles(smem);
-  const int l = threadIdx.x & 31;
-  const int64_t tile = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (tile * 16 >= B) return;
-  auto idx = [&](int r) -> int64_t {
-    const int64_t i = tile * 16 + r;
-    return random ? (int64_t)(splitmix64(seed ^ (uint64_t)i) % (uint64_t)n_rows) : i;
-  };
-  load_inputs(W.a0, X, sc, idx);
-  __syncwarp();
-  {
-    float acc[8][4];
-    layer_fwd<1, 8>(W.a0, kS16, N.W1, kS16, N.b1, acc);
-    store_relu<8>(acc, W.a[0], kS64, nullptr, 0);
+// Forward and backward through the activations for B points on the Blackwell
+// tensor cores: 128 points per CTA, one per thread (tcgen05.mma, FP32
+// accumulators in TMEM); rows of X (raw inputs) and T (raw targets), drawn by
+// a seeded hash when random, scaled by sc.  Loss = mean over points and the
+// kOut outputs of (y_n - t_n)^2; its partial is per CTA (loss_part).  The
+// backward products take the transposed weights as K-major operands (row n:
+// the weights from input n to every output), so that every operand is
+// K-major.  Stored for the weight gradients: the bf16 inputs and hidden
+// activations, the FP32 output gradient and hidden pre-activation gradients.  A wait on the tensor core that gives up
+// sets *status to PDN_E_TIMEOUT.
+struct TrainTcSmem {
+  UmmaNet N;                               // forward weights (K-major) and biases
+  __nv_bfloat16 W4T[kHid * kOutPad];       // [64 inputs][16 outputs]
+  __nv_bfloat16 W3T[kHid * kHid];          // [64 inputs][64 outputs]
+  __nv_bfloat16 W2T[kHid * kHid];
+  UmmaTile T;                              // inputs, hidden activations, barrier, TMEM address
+  __nv_bfloat16 g16[kTcRows * kOutPad];    // output gradient
+  __nv_bfloat16 g64[kTcRows * kHid];       // hidden gradient
+  float red[kTcRows / 32];
+};
+static_assert(sizeof(UmmaNet) % 16 == 0 && sizeof(UmmaTile) % 16 == 0, "16-byte aligned operand tiles");
+
+__device__ inline void load_net_transposed(TrainTcSmem &S, const float *p) {
+  const float *W2 = p + kHid * kIn + kHid, *W3 = W2 + kHid * kHid + kHid, *W4 = W3 + kHid * kHid + kHid;
+  for (int i = threadIdx.x; i < kHid * kOutPad; i += blockDim.x) {
+    const int n = i / kOutPad, k = i % kOutPad;  // n: input of layer 4, k: its output
+    S.W4T[umma::core_offset(n, k, kOutPad) / 2] = __float2bfloat16_rn(k < kOut ? W4[k * kHid + n] : 0.0f);
   }
-  __syncwarp();
-  {
-    float acc[8][4];
-    layer_fwd<4, 8>(W.a[0], kS64, N.W2, kS64, N.b2, acc);
-    store_relu<8>(acc, W.a[1], kS64, nullptr, 0);
-  }
-  __syncwarp();
-  {
-    float acc[8][4];
-    layer_fwd<4, 8>(W.a[1], kS64, N.W3, kS64, N.b3, acc);
-    store_relu<8>(acc, W.a[2], kS64, nullptr, 0);
-  }
-  __syncwarp();
-  {
-    float acc[2][4];
-    layer_fwd<4, 2>(W.a[2], kS64, N.W4, kS64, N.b4, acc);
-    store_f32<2>(acc, W.y, kOutPad);
-  }
-  __syncwarp();
-  // output gradient dL/dy_n = 2 (y_n - t_n) / (B kOut), padded columns 0
-  const float gscale = 2.0f / ((float)B * (float)kOut);
-  float lsum = 0.0f;
-  for (int e = l; e < 16 * kOutPad; e += 32) {
-    const int r = e / kOutPad, c = e % kOutPad;
-    float gv = 0.0f;
-    if (c < kOut) {
-      const float tn = (T[idx(r) * kOut + c] - sc.out_shift[c]) / sc.out_mul[c];
-      const float dlt = W.y[r * kOutPad + c] - tn;
-      lsum += dlt * dlt;
-      gv = gscale * dlt;
-    }
-    tb.DY[(tile * 16 + r) * kOutPad + c] = gv;
-    W.g16[r * kS16 + c] = __float2bfloat16_rn(gv);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-  if (l == 0) tb.loss_part[tile] = lsum / ((float)B * (float)kOut);
-  // the activations for the weight gradients
-  for (int e = l; e < 16 * kInPad; e += 32) {
-    const int r = e / kInPad, c = e % kInPad;
-    tb.A0[(tile * 16 + r) * kInPad + c] = W.a0[r * kS16 + c];
-  }
-  for (int k = 0; k < 3; ++k)
-    for (int e = l; e < 16 * kHid; e += 32) {
-      const int r = e / kHid, c = e % kHid;
-      tb.A[k][(tile * 16 + r) * kHid + c] = W.a[k][r * kS64 + c];
-    }
-  __syncwarp();
-  float *dz3 = tb.DZ[2] + tile * 16 * kHid, *dz2 = tb.DZ[1] + tile * 16 * kHid, *dz1 = tb.DZ[0] + tile * 16 * kHid;
-  {
-    float acc[8][4];
-    layer_back<1, 8>(W.g16, kS16, N.W4, kS64, acc);
-    store_grad<8>(acc, W.a[2], dz3, W.g64, kS64);
-  }
-  __syncwarp();
-  {
-    float acc[8][4];
-    layer_back<4, 8>(W.g64, kS64, N.W3, kS64, acc);
-    __syncwarp();  // every lane has read the gradient tile before it is overwritten
-    store_grad<8>(acc, W.a[1], dz2, W.g64, kS64);
-  }
-  __syncwarp();
-  {
-    float acc[8][4];
-    layer_back<4, 8>(W.g64, kS64, N.W2, kS64, acc);
-    __syncwarp();
-    store_grad<8>(acc, W.a[0], dz1, W.g64, kS64);
+  for (int i = threadIdx.x; i < kHid * kHid; i += blockDim.x) {
+    const int n = i / kHid, k = i % kHid;
+    S.W3T[umma::core_offset(n, k, kHid) / 2] = __float2bfloat16_rn(W3[k * kHid + n]);
+    S.W2T[umma::core_offset(n, k, kHid) / 2] = __float2bfloat16_rn(W2[k * kHid + n]);
   }
 }
 
-// Weight and bias gradients of one layer over one chunk of kChunk points:
-// dW[n][k] = sum_m dZ[m][n] A[m][k], db[n] = sum_m dZ[m][n], in a fixed
-// order, written as the chunk's partial.
-__global__ void __launch_bounds__(kWarps * 32) k_train_wgrad(TrainBufs tb, int64_t B, float *partW, float *partB,
-                                                             int64_t n_chunks) {
-  __shared__ __align__(16) __nv_bfloat16 sG[kChunk * kS64];
-  __shared__ __align__(16) __nv_bfloat16 sA[kChunk * kS64];
+__global__ void __launch_bounds__(kTcRows) k_train_tiles_tc(const float *params, Scaling sc, const float *X,
+                                                            const float *Tgt, int64_t n_rows, int64_t B,
+                                                            int32_t random, uint64_t seed, TrainBufs tb,
+                                                            int32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  TrainTcSmem &S = *reinterpret_cast<TrainTcSmem *>(smem);
+  const int t = threadIdx.x;
+  load_net_umma(S.N, params);
+  load_net_transposed(S, params);
+  const int64_t row = (int64_t)blockIdx.x * kTcRows + t;  // B is a multiple of 128
+  const int64_t src = random ? (int64_t)(splitmix64(seed ^ (uint64_t)row) % (uint64_t)n_rows) : row;
+  {
+    float xn[kInPad];
+#pragma unroll
+    for (int c = 0; c < kInPad; ++c) xn[c] = c < kIn ? (X[src * kIn + c] - sc.in_shift[c]) * sc.in_mul[c] : 0.0f;
+    uint4 lo, hi;
+    tc_store16(S.T.x, kInPad, t, 0, xn, lo, hi);
+    uint4 *dst = reinterpret_cast<uint4 *>(tb.A0 + row * kInPad);
+    dst[0] = lo;
+    dst[1] = hi;
+  }
+  tc_setup(S.T);
+  uint32_t phase = 0;
+  float y[kOutPad];
+  bool ok = tc_forward128(S.N, S.T, phase, y, [&](int L, int c, const uint4 &lo, const uint4 &hi) {
+    uint4 *dst = reinterpret_cast<uint4 *>(tb.A[L] + row * kHid + c);
+    dst[0] = lo;
+    dst[1] = hi;
+  });
+  float lsum = 0.0f;
+  if (ok) {
+    // output gradient dL/dy_n = 2 (y_n - t_n) / (B kOut), padded columns 0
+    const float gscale = 2.0f / ((float)B * (float)kOut);
+    float g[16];
+#pragma unroll
+    for (int c = 0; c < kOutPad; ++c) {
+      float gv = 0.0f;
+      if (c < kOut) {
+        const float tn = (Tgt[src * kOut + c] - sc.out_shift[c]) / sc.out_mul[c];
+        const float dlt = y[c] - tn;
+        lsum += dlt * dlt;
+        gv = gscale * dlt;
+      }
+      g[c] = gv;
+      tb.DY[row * kOutPad + c] = gv;
+    }
+    uint4 lo, hi;
+    tc_store16(S.g16, kOutPad, t, 0, g, lo, hi);
+    // backward through the hidden layers: dZ_L = (G W_{L+1}) * relu'(a_L)
+#pragma unroll 1
+    for (int L = 2; L >= 0 && ok; --L) {
+      const __nv_bfloat16 *A = L == 2 ? S.g16 : S.g64;
+      const __nv_bfloat16 *Bt = L == 2 ? S.W4T : (L == 1 ? S.W3T : S.W2T);
+      const uint32_t col = (uint32_t)(L & 1) * 64u;
+      ok = tc_mma128(A, Bt, L == 2 ? kOutPad : kHid, kHid, S.T.tmem + col, S.T, phase);
+      if (!ok) break;
+#pragma unroll 1
+      for (int c = 0; c < kHid; c += 16) {
+        float v[16];
+        umma::tmem_ld16(tc_lane(S.T, col + (uint32_t)c), v);
+        const __nv_bfloat16 *act = tb.A[L] + row * kHid + c;
+        float *dz = tb.DZ[L] + row * kHid + c;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          v[k] = __bfloat162float(act[k]) > 0.0f ? v[k] : 0.0f;
+          dz[k] = v[k];
+        }
+        tc_store16(S.g64, kHid, t, c, v, lo, hi);
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if ((t & 31) == 0) S.red[t >> 5] = lsum;
+  __syncthreads();
+  if (t == 0) {
+    float tot = 0.0f;
+    for (int w = 0; w < kTcRows / 32; ++w) tot += S.red[w];
+    tb.loss_part[blockIdx.x] = tot / ((float)B * (float)kOut);
+    if (!ok) atomicExch(status, PDN_E_TIMEOUT);
+  }
+  tc_teardown(S.T);
+}
+
+// Weight and bias gradients of one layer over one chunk of kChunk points, on
+// the Blackwell tensor cores: one CTA per (chunk of 128 points, layer).  dW[n][k] = sum_m dZ[m][n] A[m][k] is the MMA
+// D[n][k] = sum over K = the 128 points of dZ^T[n][m] A^T[k][m]: both
+// operands are staged transposed (rows n and k, the points along K), rows of
+// the 128-row A operand past the layer's outputs are zero.  Lane n of TMEM
+// then holds dW[n][:] for thread n.  The bias gradient is the fixed-order
+// FP32 sum of dZ over the chunk as before.
+struct WgradTcSmem {
+  __nv_bfloat16 gT[kTcRows * kChunk];    // dZ^T [128 (outputs, padded)][128 points]
+  __nv_bfloat16 aT[kHid * kChunk];       // A^T [64 (inputs)][128 points]
+  UmmaTile T;                            // barrier and TMEM address (its tiles unused)
+};
+
+__global__ void __launch_bounds__(kTcRows) k_train_wgrad_tc(TrainBufs tb, int64_t B, float *partW, float *partB,
+                                                            int64_t n_chunks, int32_t *status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  WgradTcSmem &S = *reinterpret_cast<WgradTcSmem *>(smem);
   const int layer = blockIdx.y;
   const int64_t chunk = blockIdx.x;
   const int M = layer_out(layer), K = layer_in(layer);
   const float *dz = layer == 3 ? tb.DY : tb.DZ[layer];
   const __nv_bfloat16 *act = layer == 0 ? tb.A0 : tb.A[layer - 1];
+  const int t = threadIdx.x;
   const int64_t r0 = chunk * kChunk;
-  for (int e = threadIdx.x; e < kChunk * M; e += blockDim.x) {
-    const int r = e / M, c = e % M;
-    sG[r * kS64 + c] = __float2bfloat16_rn(dz[(r0 + r) * M + c]);
+  unsigned char *gb = reinterpret_cast<unsigned char *>(S.gT), *ab = reinterpret_cast<unsigned char *>(S.aT);
+  // thread t stages point t: its M gradients into column t of dZ^T, its K
+  // activations into column t of A^T; rows of dZ^T past M are zero
+  for (int n = 0; n < kTcRows; ++n) {
+    const float v = n < M ? dz[(r0 + t) * M + n] : 0.0f;
+    *reinterpret_cast<__nv_bfloat16 *>(gb + umma::core_offset(n, t, kChunk)) = __float2bfloat16_rn(v);
   }
-  for (int e = threadIdx.x; e < kChunk * K; e += blockDim.x) {
-    const int r = e / K, c = e % K;
-    sA[r * kS64 + c] = act[(r0 + r) * K + c];
-  }
-  __syncthreads();
+  for (int k = 0; k < K; ++k)
+    *reinterpret_cast<__nv_bfloat16 *>(ab + umma::core_offset(k, t, kChunk)) = act[(r0 + t) * K + k];
+  tc_setup(S.T);
+  uint32_t phase = 0;
+  const bool ok = tc_mma128(S.gT, S.aT, kChunk, K, S.T.tmem, S.T, phase);
   float *pW = partW + ((size_t)layer * n_chunks + chunk) * (kHid * kHid);
   float *pB = partB + ((size_t)layer * n_chunks + chunk) * kHid;
-  for (int c = threadIdx.x; c < M; c += blockDim.x) {
-    float sb = 0.0f;
-    for (int r = 0; r < kChunk; ++r) sb += dz[(r0 + r) * M + c];
-    pB[c] = sb;
-  }
-  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, g = l >> 2, t = l & 3;
-  const int mt_n = M / 16, nt_n = K / 8;
-  for (int tl = w; tl < mt_n * nt_n; tl += kWarps) {
-    const int n0 = (tl / nt_n) * 16, k0 = (tl % nt_n) * 8;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int s0 = 0; s0 < kChunk; s0 += 16) {
-      uint32_t a[4], b[2];
-      // A = dZ^T (rows: outputs n, columns: points), from dZ stored by point
-      ldsm_x4_t(a, sG + (s0 + (l & 7) + ((l >> 4) & 1) * 8) * kS64 + n0 + ((l >> 3) & 1) * 8);
-      // B = A_prev (rows: points, columns: inputs k)
-      ldsm_x2_t(b, sA + (s0 + (l & 15)) * kS64 + k0);
-      mma16816(acc, a, b);
+  if (ok) {
+#pragma unroll 1
+    for (int c = 0; c < K; c += 16) {
+      float v[16];
+      umma::tmem_ld16(tc_lane(S.T, (uint32_t)c), v);
+      if (t < M) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) pW[t * K + c + k] = v[k];
+      }
     }
-    pW[(n0 + g) * K + k0 + 2 * t] = acc[0];
-    pW[(n0 + g) * K + k0 + 2 * t + 1] = acc[1];
-    pW[(n0 + g + 8) * K + k0 + 2 * t] = acc[2];
-    pW[(n0 + g + 8) * K + k0 + 2 * t + 1] = acc[3];
   }
+  if (t < M) {
+    float sb = 0.0f;
+    for (int r = 0; r < kChunk; ++r) sb += dz[(r0 + r) * M + t];
+    pB[t] = sb;
+  }
+  if (!ok && t == 0) atomicExch(status, PDN_E_TIMEOUT);
+  tc_teardown(S.T);
 }
 
 // Parameter p of the exchange order -> (layer, row, column or -1 for a bias).
@@ -468,7 +428,7 @@ struct HexSurSmem {
 };
 constexpr size_t kHexSurSmem = sizeof(HexSurSmem);
 static_assert(sizeof(Scaling) == PDN_SUR_SCALING * sizeof(float), "scaling record of 60 floats");
-static_assert(sizeof(SmemNet) % 16 == 0 && sizeof(Scaling) % 16 == 0, "16-byte aligned shared tiles");
+static_assert(sizeof(Scaling) % 16 == 0, "16-byte aligned shared tiles");
 
 __global__ void __launch_bounds__(kHexSurBlock, 3) k_hex_sur(Dev<float> D, Mat<float> M) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -694,7 +654,6 @@ int scuda(pdn_surrogate *s, cudaError_t e, const char *where) {
     if (_e != cudaSuccess) return scuda(s, _e, where); \
   } while (0)
 
-constexpr size_t kTileSmem = sizeof(SmemNet) + kWarps * sizeof(WarpTiles);
 
 void free_bufs(pdn_surrogate *s) {
   cudaFree(s->tb.A0);
@@ -734,11 +693,12 @@ int train_step(pdn_surrogate *s, const Scaling &sc, const float *X, const float 
                int random, uint64_t seed, float lr, float *grad_out, double *loss_out) {
   int rc = ensure_bufs(s, B);
   if (rc) return rc;
-  const int64_t tiles = B / 16, nch = B / kChunk;
-  k_train_tiles<<<(unsigned)((tiles + kWarps - 1) / kWarps), kWarps * 32, kTileSmem, s->stream>>>(
-      s->params, sc, X, T, n_rows, B, random, seed, s->tb);
+  const int64_t tiles = B / kTcRows, nch = B / kChunk;
+  k_train_tiles_tc<<<(unsigned)tiles, kTcRows, sizeof(TrainTcSmem), s->stream>>>(s->params, sc, X, T, n_rows, B,
+                                                                                random, seed, s->tb, s->status_dev);
   PS_CU(cudaGetLastError(), "train tiles");
-  k_train_wgrad<<<dim3((unsigned)nch, kLayers), kWarps * 32, 0, s->stream>>>(s->tb, B, s->partW, s->partB, nch);
+  k_train_wgrad_tc<<<dim3((unsigned)nch, kLayers), kTcRows, sizeof(WgradTcSmem), s->stream>>>(
+      s->tb, B, s->partW, s->partB, nch, s->status_dev);
   PS_CU(cudaGetLastError(), "weight gradients");
   float bc1 = 1.0f, bc2 = 1.0f;
   if (lr > 0.0f) {
@@ -854,10 +814,12 @@ static int pdn_sur_create_body(pdn_surrogate **out, const pdn_material *mat, dou
   cudaMemsetAsync(s->m1, 0, sizeof(float) * kNumParams, s->stream);
   cudaMemsetAsync(s->m2, 0, sizeof(float) * kNumParams, s->stream);
   k_init_params<<<(kNumParams + 255) / 256, 256, 0, s->stream>>>(s->params, seed);
-  if (cudaFuncSetAttribute(k_train_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem) !=
+  if (cudaFuncSetAttribute(k_sur_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSurTcSmem) !=
           cudaSuccess ||
-      cudaFuncSetAttribute(k_sur_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSurTcSmem) !=
-          cudaSuccess)
+      cudaFuncSetAttribute(k_train_tiles_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(TrainTcSmem)) != cudaSuccess ||
+      cudaFuncSetAttribute(k_train_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(WgradTcSmem)) != cudaSuccess)
     return bad(PDN_E_CUDA, "shared-memory attribute");
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bad(PDN_E_CUDA, "surrogate init");
   *out = s;
@@ -995,6 +957,7 @@ int pdn_sur_train(pdn_surrogate *s, int64_t iters, int32_t batch, double lr, uin
   std::vector<double> lh;
   double *ld = nullptr;
   if (loss) PS_CU(cudaMalloc(&ld, sizeof(double) * std::max<int64_t>(iters, 1)), "loss buffer");
+  PS_CU(cudaMemsetAsync(s->status_dev, 0, sizeof(int32_t), s->stream), "status");
   for (int64_t it = 0; it < iters; ++it) {
     const double frac = iters > 1 ? (double)it / (double)(iters - 1) : 0.0;
     const double lr_it = lr * (0.01 + 0.99 * 0.5 * (1.0 + std::cos(M_PI * frac)));
@@ -1006,10 +969,13 @@ int pdn_sur_train(pdn_surrogate *s, int64_t iters, int32_t batch, double lr, uin
     }
   }
   cudaError_t e = cudaSuccess;
+  int32_t st = 0;
   if (ld && iters > 0) e = cudaMemcpyAsync(loss, ld, sizeof(double) * iters, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, s->status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   cudaFree(ld);
   if (e != cudaSuccess) return scuda(s, e, "training");
+  if (st) return sfail(s, st, "training: a bounded wait on the tensor core gave up");
   return PDN_OK;
 }
 
@@ -1022,16 +988,21 @@ int pdn_sur_gradient(pdn_surrogate *s, const float *xn, const float *tn, int64_t
   if (e == cudaSuccess) e = cudaMemcpyAsync(dx, xn, sizeof(float) * kIn * n, cudaMemcpyHostToDevice, s->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tn, sizeof(float) * kOut * n, cudaMemcpyHostToDevice, s->stream);
   int rc = PDN_OK;
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->status_dev, 0, sizeof(int32_t), s->stream);
   if (e == cudaSuccess) rc = train_step(s, identity_scaling(), dx, dt, n, n, 0, 0, 0.0f, s->grad, s->loss_dev);
   if (e == cudaSuccess && rc == PDN_OK)
     e = cudaMemcpyAsync(grad, s->grad, sizeof(float) * kNumParams, cudaMemcpyDeviceToHost, s->stream);
   double lh = 0.0;
+  int32_t st = 0;
   if (e == cudaSuccess && rc == PDN_OK) e = cudaMemcpyAsync(&lh, s->loss_dev, sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && rc == PDN_OK)
+    e = cudaMemcpyAsync(&st, s->status_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   cudaFree(dx);
   cudaFree(dt);
   if (rc) return rc;
   if (e != cudaSuccess) return scuda(s, e, "gradient");
+  if (st) return sfail(s, st, "gradient: a bounded wait on the tensor core gave up");
   if (loss) *loss = lh;
   return PDN_OK;
 }
