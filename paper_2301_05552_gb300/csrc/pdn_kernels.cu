@@ -50,21 +50,12 @@ __global__ void __launch_bounds__(kActRun) k_contact(Dev<T> D) {
   if (D.act_cnt != nullptr && threadIdx.x == 0) D.act_cnt[blockIdx.x] = c;
 }
 
-// Blocks take the element and node ranges from the top: the contact zone
-// and the damage under the striker sit in the top layers, the highest ids of
-// a layered plate, and their slow warps (the full law, the contact reaction)
-// then run in the first waves of the launch instead of trailing behind the
-// last one.  Each block's range is the same as in ascending order.
-__device__ __forceinline__ int64_t item_from_top() {
-  return (int64_t)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
-}
-
 template <typename T, bool BOX, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_hex(Dev<T> D, Mat<T> M) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  hex_item<T, BOX>(D, M, item_from_top(), mode);
+  hex_item<T, BOX>(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 template <typename T, bool FLAT, int MINB>
@@ -72,7 +63,7 @@ __global__ void __launch_bounds__(128, MINB) k_coh(Dev<T> D, Mat<T> M) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  coh_item<T, FLAT>(D, M, item_from_top(), mode);
+  coh_item<T, FLAT>(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 // Hex and interface elements in one launch: blocks alternate between a tile
@@ -107,7 +98,7 @@ __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
-  gather_item(D, item_from_top(), mode);
+  gather_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 // Kernel 5: the tail of a pass as its own small launch (kept out of the
