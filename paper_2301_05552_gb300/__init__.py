@@ -118,13 +118,16 @@ def build(force: bool = False) -> str:
 
 
 def lib():
-    """Load lib/libpdn.so (building it first if it is missing or stale)."""
+    """Load lib/libpdn.so (building it first if it is missing or stale); with
+    the environment variable PDN_CHECKED=1, lib/libpdn_check.so, the build with
+    the device bounds checks (PDN_CHECK)."""
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
-            if _build._stale():
-                _build.build()
+            checked = os.environ.get("PDN_CHECKED") == "1"
+            path = _build.LIB_CHECK if checked else _build.LIB
+            if _build._stale(path):
+                _build.build(check=checked)
             if not os.path.exists(path):
                 raise RuntimeError(f"CUDA library {path} is missing; run paper_2301_05552_gb300.build()")
             L = C.CDLL(path)

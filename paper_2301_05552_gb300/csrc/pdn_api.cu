@@ -1127,7 +1127,9 @@ int pdn_step(pdn_ctx *ctx, int64_t nsteps) {
     const Ctl &c = *ctx->ctl_host;
     if (c.status) {
       return fail(ctx, c.status,
-                  c.status == PDN_E_NONFINITE  ? "non-finite acceleration or displacement"
+                  c.check == CHECK_ELEMENT_NODE   ? "device bounds check: an element names a node out of range"
+                  : c.check == CHECK_SURFACE_NODE ? "device bounds check: a surface entry names a node out of range"
+                  : c.status == PDN_E_NONFINITE   ? "non-finite acceleration or displacement"
                   : c.status == PDN_E_TIMEOUT ? "a bounded wait on the tensor core gave up (learned law)"
                                               : "contact release limit reached (Algorithm 2)");
     }

@@ -192,6 +192,24 @@ __device__ __forceinline__ void repeat_mark_nodes(uint8_t *mark, const int nd[8]
   for (int a = 0; a < 8; ++a) mark[nd[a]] = 1;
 }
 
+// PDN_CHECK builds: the eight node ids of an element lie in [0, n_nodes);
+// otherwise the first failure is recorded (CheckCode) and the caller skips
+// the element.  Always true in other builds.
+template <typename T>
+__device__ __forceinline__ bool nodes_in_range(const Dev<T> &D, const int (&nd)[8]) {
+#ifdef PDN_CHECK
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) ok = ok && nd[a] >= 0 && (int64_t)nd[a] < D.nn;
+  if (!ok) atomicCAS(&D.ctl->check, 0, (int32_t)CHECK_ELEMENT_NODE);
+  return ok;
+#else
+  (void)D;
+  (void)nd;
+  return true;
+#endif
+}
+
 // ---------------------------------------------------------------------------
 // Intralaminar law (Algorithm 4) at one Gauss point, ply axes.
 // eps: engineering strain [11 22 33 12 13 23]; h: history in/out

@@ -40,6 +40,17 @@ struct Ctl {
   double f_peak;
   int32_t nonfinite;   // set by the gather when an acceleration is not finite
   int32_t timeout;     // set by a kernel whose bounded wait on the tensor core gave up
+  int32_t check;       // first failed device bounds check of a PDN_CHECK build (CheckCode), else 0
+  int32_t pad;
+};
+
+// Device bounds checks of a library built with PDN_CHECK defined: an index
+// out of range records its code in Ctl::check, the item skips the access, and
+// the tail halts the run (PDN_E_ARG).  Without PDN_CHECK the checks compile
+// to nothing.
+enum CheckCode : int32_t {
+  CHECK_ELEMENT_NODE = 1,  // a hex or interface element names a node outside [0, n_nodes)
+  CHECK_SURFACE_NODE = 2   // a contact-surface entry names a node outside [0, n_nodes)
 };
 
 // Rigid striker (Sec. 2.2.2).  The committed part is written only by the tail

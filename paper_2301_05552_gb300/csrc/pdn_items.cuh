@@ -66,6 +66,12 @@ __device__ __forceinline__ bool contact_item(const Dev<T> &D, int64_t s, int mod
   const StrikerStep *ss = D.imp_step;
   const int64_t nn = D.nn, ns = D.ns;
   const int64_t j = D.surf_base >= 0 ? D.surf_base + s : D.surf[s];
+#ifdef PDN_CHECK
+  if (j < 0 || j >= D.nn) {
+    atomicCAS(&D.ctl->check, 0, (int32_t)CHECK_SURFACE_NODE);
+    return false;
+  }
+#endif
   const int cur = ctl->dpar;
   const int spar = (int)((ctl->step + 1) & 1), ppar = (int)(ctl->step & 1);
   double *d = D.d[cur];
@@ -202,6 +208,7 @@ __device__ __forceinline__ bool hex_box_forces(const Dev<float> &D, const Mat<fl
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (!nodes_in_range(D, nd)) return false;
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   float ua[8][3];
 #pragma unroll
@@ -465,6 +472,7 @@ __device__ __forceinline__ void hex_item(const Dev<T> &D, const Mat<T> &M, int64
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * e + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (!nodes_in_range(D, nd)) return;
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   const T *PDN_STATE_RESTRICT hin = D.hist[hb] + e;
   T *PDN_STATE_RESTRICT hout = D.hist[hb ^ 1] + e;
@@ -675,6 +683,7 @@ __device__ __forceinline__ bool coh_forces(const Dev<T> &D, const Mat<T> &M, int
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.coh) + 2 * c + 1);
   const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (!nodes_in_range(D, nd)) return false;
   if (mode == MODE_REPEAT) repeat_mark_nodes(D.rmark_n, nd);
   constexpr int QX[4] = {-1, 1, 1, -1}, QY[4] = {-1, -1, 1, 1};
   // the upper face coincides with the lower one in the reference
@@ -1103,7 +1112,10 @@ __device__ void tail_block(const Dev<T> &D, int mode) {
     nd += ti[1][k];
   }
   c.nonfinite = 0;  // for the next pass
-  if (c.timeout) {
+  if (c.check) {
+    c.status = PDN_E_ARG;
+    c.mode = MODE_HALT;
+  } else if (c.timeout) {
     c.status = PDN_E_TIMEOUT;
     c.mode = MODE_HALT;
   } else if (mode == MODE_FORCES) {

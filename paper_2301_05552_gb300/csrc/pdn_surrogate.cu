@@ -456,7 +456,14 @@ __global__ void __launch_bounds__(kHexSurBlock, 3) k_hex_sur(Dev<float> D, Mat<f
   const float4 *__restrict__ U = D.u4[ub];
   const int4 c0 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * el);
   const int4 c1 = __ldg(reinterpret_cast<const int4 *>(D.hex) + 2 * el + 1);
-  const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+  if (!nodes_in_range(D, nd)) {
+    // PDN_CHECK build: the element is skipped (its CTA still takes part in
+    // every network evaluation)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) nd[a] = 0;
+    act = false;
+  }
   const float *__restrict__ hin = D.hist[hb] + el;
   float *__restrict__ hout = D.hist[hb ^ 1] + el;
   const bool pristine_in = D.pflag[0] != nullptr && D.pflag[hb][el] != 0;
