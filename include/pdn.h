@@ -173,12 +173,23 @@ typedef struct {
                               8 x 8 or 8 x 4 columns: one kernel evaluates the elements
                               layer by layer and updates every node inside a tile from
                               shared memory; only tile-boundary nodes go through the
-                              element-force slots.  Planned by pdn_init_mesh where the
-                              mesh allows it and kept by the autotuner of the first
-                              pdn_step when it is faster.  The environment variable
-                              PDN_SWEEP=0, read by pdn_init_mesh, keeps the separate
-                              kernels; PDN_SWEEP=1, read by the first pdn_step, keeps
-                              the sweep whatever the timing */
+                              element-force slots.  Planned by pdn_init_mesh only when the
+                              environment variable PDN_SWEEP=1 is set there and the mesh
+                              allows it (it measured slower than the separate kernels),
+                              and kept by the first pdn_step while PDN_SWEEP=1 is still
+                              set; a planned sweep keeps the interface elements
+                              (coh_pairs 0) */
+  int32_t coh_pairs;       /* 1: interfaces evaluated as node pairs inside the gather (flat
+                              interfaces, at most eight elements per node, no column sweep):
+                              with Newton-Cotes points at the corners (Sec. 2.3.2) the
+                              traction at a point depends only on the jump of the two
+                              coincident nodes there, so the law is evaluated once per node
+                              and each incident element's share added in CSR order, with
+                              the same sums as the interface kernel; no interface kernel
+                              runs.  0: interface elements (k_coh).  The environment
+                              variable PDN_COH_PAIRS=0, read by pdn_init_mesh, keeps the
+                              interface elements */
+  int32_t reserved;
   double tune_ms[12];      /* mean time of an internal-force pass with each variant when
                               tuned (0 if not): entries 0..3 the hex variants with separate
                               kernels, entry 8 the column sweep (0 where none was planned);

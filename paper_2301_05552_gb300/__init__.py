@@ -96,7 +96,8 @@ class Info(C.Structure):
                 ("f_peak", C.c_double), ("step", C.c_int64), ("n_active", C.c_int64), ("n_repeats", C.c_int64),
                 ("n_nodes", C.c_int64), ("n_hex", C.c_int64), ("n_coh", C.c_int64), ("n_surf", C.c_int64),
                 ("device_bytes", C.c_int64), ("status", C.c_int32), ("precision", C.c_int32),
-                ("hex_variant", C.c_int32), ("sweep", C.c_int32), ("tune_ms", C.c_double * 12)]
+                ("hex_variant", C.c_int32), ("sweep", C.c_int32), ("coh_pairs", C.c_int32),
+                ("reserved", C.c_int32), ("tune_ms", C.c_double * 12)]
 
 
 class BatchInfo(C.Structure):
@@ -414,7 +415,7 @@ def pdn_internal_force(ctx: Context):
 def pdn_get_info(ctx: Context) -> dict:
     info = Info()
     _check(ctx, lib().pdn_get_info(ctx.handle, C.byref(info)))
-    out = {k: getattr(info, k) for k, _ in Info._fields_}
+    out = {k: getattr(info, k) for k, _ in Info._fields_ if k != "reserved"}
     out["tune_ms"] = list(info.tune_ms)
     return out
 

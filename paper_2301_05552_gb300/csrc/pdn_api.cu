@@ -396,6 +396,8 @@ static int get_history_t(pdn_ctx *ctx, const Dev<T> &D, T *hist, T *rD) {
   }
   if (rD && nc > 0) {
     std::vector<uint8_t> cf(nc);
+    PDN_CU(launch_pairs_to_elements(D, ctx->stream), "interface thresholds from node pairs");
+    PDN_CU(cudaStreamSynchronize(ctx->stream), "interface thresholds from node pairs");
     PDN_CU(cudaMemcpy(rD, D.rD[hb], sizeof(T) * 4 * nc, cudaMemcpyDeviceToHost), "read interface history");
     PDN_CU(cudaMemcpy(cf.data(), D.cflag[hb], nc, cudaMemcpyDeviceToHost), "read interface flags");
     for (int64_t e = 0; e < nc; ++e)
@@ -636,14 +638,16 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       rank[e] = w;
     }
   }
-  // column sweep (FP32 box hexes, flat interfaces, eight slots per node);
-  // PDN_SWEEP=0, read here, keeps separate element and gather kernels
+  // column sweep (FP32 box hexes, flat interfaces, eight slots per node),
+  // planned only on request (PDN_SWEEP=1, read here): it measured slower
+  // than the separate kernels (400x600x32 plate: 1.59 against 1.29 ms per
+  // step), and a planned sweep keeps the interface elements
   Sweep sweep{};
   std::vector<int32_t> bnodes;
   bool sweep_on = false;
   {
     const char *sv = std::getenv("PDN_SWEEP");
-    const bool allowed = !(sv && sv[0] == '0' && sv[1] == '\0');
+    const bool allowed = sv && sv[0] == '1' && sv[1] == '\0';
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm < 1) {
@@ -652,6 +656,80 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     }
     if (allowed && opt->precision == PDN_FP32_FORCE && all_boxes && all_flat_coh && ell)
       sweep_on = plan_sweep(nn, nh, nc, mesh->hex, mesh->coh, n_sm, sweep, bnodes);
+  }
+  // Interfaces as node pairs (flat interfaces, eight slots per node, no
+  // column sweep): per node its partner across the interface, the counts of
+  // its incident hexes and interface elements, and the area weights of the
+  // latter in CSR order, in the element precision and with the interface
+  // kernel's arithmetic.  The pairing must be mutual and the same for every
+  // incident interface element of a node.  PDN_COH_PAIRS=0, read here, keeps
+  // the interface elements.
+  bool pairs_on = false, pairs_uniform = true;
+  std::vector<int2> ipair;
+  std::vector<char> iw;  // [nn] 4 weights of the element precision
+  double coh_w = 0.0;
+  {
+    const char *pv = std::getenv("PDN_COH_PAIRS");
+    const bool allowed = !(pv && pv[0] == '0' && pv[1] == '\0');
+    auto build_pairs = [&](auto tag) -> bool {
+      using T = decltype(tag);
+      ipair.assign(nn, int2{-1, 0});
+      iw.assign(sizeof(T) * 4 * nn, 0);
+      T *wn = reinterpret_cast<T *>(iw.data());
+      bool first = true;
+      T w0 = T(0);
+      for (int64_t j = 0; j < nn; ++j) {
+        int nhx = 0, kc = 0, top = 0;
+        int32_t partner = -1;
+        for (int32_t r = row[j]; r < row[j + 1]; ++r) {
+          const int32_t slot = col[r];
+          if (slot < nh * 8) {
+            if (kc) return false;  // hexes first (CSR order)
+            ++nhx;
+            continue;
+          }
+          const int64_t c = slot / 8 - nh;
+          const int a = slot % 8;
+          const int32_t *q = mesh->coh + c * 8;
+          const int32_t pj = q[a ^ 4];
+          const int tp = a >= 4 ? 1 : 0;
+          if (kc == 0) {
+            partner = pj;
+            top = tp;
+          } else if (pj != partner || tp != top || kc == 4) {
+            return false;
+          }
+          const T x0 = (T)mesh->X[q[0]], x2 = (T)mesh->X[q[2]];
+          const T y0 = (T)mesh->X[nn + q[0]], y2 = (T)mesh->X[nn + q[2]];
+          const T w = T(0.25) * (x2 - x0) * (y2 - y0);
+          wn[4 * j + kc] = w;
+          if (first) {
+            w0 = w;
+            first = false;
+          } else if (w != w0) {
+            pairs_uniform = false;
+          }
+          ++kc;
+        }
+        if (nhx > 8 || partner == (int32_t)j) return false;
+        ipair[j] = int2{partner, kc | (top << 3) | (nhx << 4)};
+      }
+      for (int64_t j = 0; j < nn; ++j) {
+        const int32_t pj = ipair[j].x;
+        if (pj >= 0 && (ipair[pj].x != (int32_t)j || ((ipair[pj].y ^ ipair[j].y) & 8) == 0)) return false;
+      }
+      coh_w = (double)w0;
+      return true;
+    };
+    if (allowed && nc > 0 && all_flat_coh && ell && !sweep_on)
+      pairs_on = opt->precision == PDN_FP64 ? build_pairs(double{}) : build_pairs(float{});
+    if (!pairs_on) {
+      std::vector<int2>().swap(ipair);
+      std::vector<char>().swap(iw);
+      pairs_uniform = true;
+    } else if (pairs_uniform) {
+      std::vector<char>().swap(iw);
+    }
   }
   // interface stable step: rho_bar = rho * h, h = volume / face area of the
   // thinner hex sharing a face with the interface element
@@ -705,6 +783,8 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   const size_t ts = fp64 ? 8 : 4;
   struct Ptrs {
     int32_t *hex, *coh, *surf, *surf_of, *row, *col, *pos, *act_cnt, *bnodes;
+    int2 *ipair;
+    char *iw, *rDn[2];
     uint32_t *rank;
     int8_t *ply;
     char *X4, *imass, *u4[2], *hist[2], *rD[2], *fe;
@@ -758,6 +838,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     P.fout = A.take<double>(sizeof(double) * 3 * nn);
     P.field = A.take<float>(sizeof(float) * std::max(nh, nc1));
     P.bnodes = A.take<int32_t>(sizeof(int32_t) * std::max<size_t>(bnodes.size(), 1));
+    P.ipair = A.take<int2>(sizeof(int2) * std::max<size_t>(ipair.size(), 1));
+    P.iw = A.take<char>(std::max<size_t>(iw.size(), 16));
+    for (int b = 0; b < 2; ++b) P.rDn[b] = A.take<char>(pairs_on ? ts * nn : 16);
   };
   Arena probe;
   layout(probe);
@@ -846,6 +929,11 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   chk(up(P.pos, pos.data(), sizeof(int32_t) * pos.size()));
   chk(up(P.rank, rank.data(), sizeof(uint32_t) * rank.size()));
   if (sweep_on) chk(up(P.bnodes, bnodes.data(), sizeof(int32_t) * bnodes.size()));
+  if (pairs_on) {
+    chk(up(P.ipair, ipair.data(), sizeof(int2) * ipair.size()));
+    chk(up(P.iw, iw.data(), iw.size()));
+    for (int b = 0; b < 2; ++b) chk(cudaMemset(P.rDn[b], 0, ts * nn));
+  }
   chk(up(d_mass, mass.data(), sizeof(double) * nn));
   chk(up(d_imass, imass.data(), imass.size()));
   for (int b = 0; b < 2; ++b) {
@@ -930,6 +1018,10 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     D.rmark_e = (full || sweep_on) ? nullptr : d_rmark_e;
     D.rmark_n = (full || sweep_on) ? nullptr : d_rmark_n;
     D.sweep = nullptr;
+    D.ipair = pairs_on ? P.ipair : nullptr;
+    D.iw = (pairs_on && !pairs_uniform) ? reinterpret_cast<const V4 *>(P.iw) : nullptr;
+    D.coh_w = (T)coh_w;
+    for (int b = 0; b < 2; ++b) D.rDn[b] = pairs_on ? reinterpret_cast<T *>(P.rDn[b]) : nullptr;
     D.nrm = d_nrm;
     D.lam = d_lam;
     D.trial = d_trial;
@@ -1399,6 +1491,8 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
   info->precision = ctx->precision;
   info->hex_variant = ctx->precision == PDN_FP64 ? ctx->Dd.hex_variant : ctx->Df.hex_variant;
   info->sweep = (ctx->precision == PDN_FP32_FORCE && ctx->Df.sweep != nullptr) ? 1 + ctx->sweep.tile : 0;
+  info->coh_pairs = (ctx->precision == PDN_FP64 ? ctx->Dd.ipair : ctx->Df.ipair) != nullptr ? 1 : 0;
+  info->reserved = 0;
   for (int v = 0; v < 12; ++v) info->tune_ms[v] = ctx->tune_ms[v];
   return PDN_OK;
 }

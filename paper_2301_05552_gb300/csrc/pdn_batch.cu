@@ -774,6 +774,10 @@ static int pdn_batch_init_body(pdn_batch **out, int32_t n_plates, const pdn_mesh
   for (int p = 0; p < n_plates; ++p) {
     int rc = pdn_init_mesh(&b->plates[p], &meshes[p], &mats[p], &o);
     if (rc) return fail_init(rc, "plate " + std::to_string(p) + ": " + pdn_last_error(nullptr));
+    // the batched kernel evaluates interface elements, so the plate keeps
+    // their thresholds in the element layout (no node pairs)
+    b->plates[p]->Df.ipair = nullptr;
+    b->plates[p]->Dd.ipair = nullptr;
   }
   int rc = b->precision == PDN_FP64 ? upload_records<double>(b) : upload_records<float>(b);
   if (rc) return fail_init(rc, b->err);

@@ -220,6 +220,10 @@ template <typename T>
 int energies_t(pdn_ctx *ctx, const Dev<T> &D, double out[6]) {
   const int nbn = blocks_of(D.nn), nbh = blocks_of(D.nh), nbc = D.nc > 0 ? blocks_of(D.nc) : 0;
   double *part = D.fout;  // 3 nn doubles: room for 2 nbn + nbh + nbc partials
+  if (nbc > 0) {
+    const cudaError_t ep = launch_pairs_to_elements(D, ctx->stream);
+    if (ep != cudaSuccess) return ctx_cuda_fail(ctx, ep, "interface thresholds from node pairs");
+  }
   k_energy_nodes<T><<<nbn, kBlock, 0, ctx->stream>>>(D, part, part + nbn);
   if (D.nh > 0) k_energy_hex<T><<<nbh, kBlock, 0, ctx->stream>>>(D, ctx->Md, part + 2 * nbn);
   if (nbc > 0) k_energy_coh<T><<<nbc, kBlock, 0, ctx->stream>>>(D, ctx->Md, part + 2 * nbn + nbh);

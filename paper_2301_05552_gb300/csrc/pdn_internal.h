@@ -225,6 +225,26 @@ struct Dev {
   // per node), or nullptr for separate element and gather kernels; a host
   // pointer, read only by the launcher
   const Sweep *sweep;
+  // Interfaces as node pairs.  With Newton-Cotes points at the corners and
+  // the global frame of flat interfaces, the traction at a point of an
+  // interface element depends only on the displacement jump of the two
+  // coincident nodes there (and the point's threshold r_D), and every
+  // element sharing that node pair sees the same jump and the same history.
+  // The gather then evaluates the cohesive law once per node and adds each
+  // incident element's share w tau in CSR order, with no interface kernel
+  // and no interface slots.  Per node {partner node or -1, meta}: meta bits
+  // 0-2 incident interface elements, bit 3 the node is on the upper face,
+  // bits 4-7 incident hexes (their slots come first).  nullptr: interface
+  // elements (k_coh).
+  const int2 *ipair;
+  // area weights of the incident interface elements in CSR order ([nn]),
+  // or nullptr when every weight equals coh_w
+  const V4 *iw;
+  T coh_w;
+  // threshold r_D of each node pair, stored at its lower node ([nn],
+  // double-buffered with the history); the element layout rD/cflag is
+  // written from it only for the readers (history, energy, damage field)
+  T *rDn[2];
 };
 
 // Launchers (pdn_kernels.cu).
@@ -238,5 +258,9 @@ cudaError_t launch_hex_sur(const Dev<float> &D, const Mat<float> &M, cudaStream_
 template <typename T>
 cudaError_t launch_damage_field(const Dev<T> &D, const Mat<T> &M, int which, float *out,
                                 cudaStream_t s);
+// Interfaces as node pairs: writes the element layout of the committed
+// interface thresholds (rD, cflag) from the pairs' (no-op otherwise).
+template <typename T>
+cudaError_t launch_pairs_to_elements(const Dev<T> &D, cudaStream_t s);
 
 }  // namespace pdn

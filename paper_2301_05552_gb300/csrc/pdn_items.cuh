@@ -158,9 +158,21 @@ __device__ __forceinline__ bool contact_item(const Dev<T> &D, int64_t s, int mod
       u.w = T(0);
       D.u4[cur][j] = u;
       D.act[spar][s] = 0;
-      // the elements of the released node are evaluated again
-      if (D.rmark_e != nullptr)
-        for (int k = D.row[j], k1 = D.row[j + 1]; k < k1; ++k) D.rmark_e[D.col[k] >> 3] = 1;
+      // the elements of the released node are evaluated again; with
+      // interfaces as node pairs its hexes, and the node on the other side of
+      // its interface pair (whose jump changed) in the gather
+      if (D.rmark_e != nullptr) {
+        if (D.ipair == nullptr) {
+          for (int k = D.row[j], k1 = D.row[j + 1]; k < k1; ++k) D.rmark_e[D.col[k] >> 3] = 1;
+        } else {
+          for (int k = D.row[j], k1 = D.row[j + 1]; k < k1; ++k) {
+            const int32_t e = D.col[k] >> 3;
+            if (e < D.nh) D.rmark_e[e] = 1;
+          }
+          const int32_t partner = D.ipair[j].x;
+          if (partner >= 0) D.rmark_n[partner] = 1;
+        }
+      }
       return false;
     }
     return on;
@@ -1326,6 +1338,91 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
         fy += f[k].y;
         fz += f[k].z;
       }
+  }
+  node_update(D, j, mode, q, fx, fy, fz);
+}
+
+// Products that no multiply-add contraction may absorb: the interface
+// shares below must round exactly as the stored slots of the element path.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// The gather of one node when interfaces are node pairs (Dev::ipair).  The
+// node's hex slots come in the first load round with its state (the first
+// four always, the rest when it has more hexes); an interface node then reads
+// its own and its partner's displacement mirror and the pair's threshold,
+// evaluates the cohesive law (Algorithm 5) once for the Newton-Cotes point
+// that the pair forms in each incident interface element (Sec. 2.3.2), and
+// adds each element's share w tau (upper node) or -w tau (lower node) in CSR
+// order: the sums of the interface kernel's slots, in the same order and
+// rounding.  The lower node writes the pair's new threshold; an undamaged
+// pair (r_D = 0 before and after) in a new step writes nothing, since the
+// other buffer then holds 0 as well (r_D never decreases, and only the
+// passes of the step write it).
+template <typename T>
+__device__ __forceinline__ void gather_pair_item(const Dev<T> &D, const Mat<T> &M, int64_t j, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  if (j >= D.nn) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_n, j)) return;
+  NodeState<T> q;
+  node_state_load(D, j, mode, q);
+  const int2 ip = D.ipair[j];
+  const V4 *fs = D.fe + 8 * j;
+  V4 f[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) f[k] = fs[k];
+  const int nhx = (ip.y >> 4) & 15;
+#pragma unroll
+  for (int k = 4; k < 8; ++k)
+    if (k < nhx) f[k] = fs[k];
+  T fx = T(0), fy = T(0), fz = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (k < nhx) {
+      fx += f[k].x;
+      fy += f[k].y;
+      fz += f[k].z;
+    }
+  if (ip.x >= 0) {
+    const Ctl *ctl = D.ctl;
+    const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+    const int hb = ctl->hpar;
+    const bool top = (ip.y >> 3) & 1;
+    const int64_t lo = top ? (int64_t)ip.x : j;
+    const V4 us = D.u4[ub][j], up = D.u4[ub][ip.x];
+    const T rin = D.rDn[hb][lo];
+    T w[4];
+    if (D.iw != nullptr) {
+      const V4 wv = D.iw[j];
+      w[0] = wv.x;
+      w[1] = wv.y;
+      w[2] = wv.z;
+      w[3] = wv.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[k] = D.coh_w;
+    }
+    const V4 ut = top ? us : up, ul = top ? up : us;
+    const T dl[3] = {ut.x - ul.x, ut.y - ul.y, ut.z - ul.z};
+    T tau[3], r1;
+    czm(M, dl, rin, r1, tau);
+    const int kc = ip.y & 7;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < kc) {
+        const T tx = mul_rn(w[k], tau[0]), ty = mul_rn(w[k], tau[1]), tz = mul_rn(w[k], tau[2]);
+        if (top) {
+          fx += tx;
+          fy += ty;
+          fz += tz;
+        } else {
+          fx -= tx;
+          fy -= ty;
+          fz -= tz;
+        }
+      }
+    if (!top && (mode == MODE_REPEAT || (mode == MODE_ADVANCE && (rin != T(0) || r1 != T(0)))))
+      D.rDn[hb ^ 1][j] = r1;
   }
   node_update(D, j, mode, q, fx, fy, fz);
 }

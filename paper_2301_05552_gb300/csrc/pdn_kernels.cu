@@ -101,6 +101,34 @@ __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
   gather_item(D, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
+// Kernel 4 with interfaces as node pairs: the gather also evaluates the
+// cohesive law of each interface node pair (no interface kernel runs).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_pairs(Dev<T> D, Mat<T> M) {
+  pdl_enter();
+  const int mode = D.ctl->mode;
+  if (mode >= MODE_DONE) return;
+  gather_pair_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
+}
+
+// The element layout of the interface thresholds (rD, cflag at the
+// committed history parity) from the node pairs' thresholds, for the readers
+// of that layout (history read-back, energy ledger, damage field).
+template <typename T>
+__global__ void k_pairs_to_elements(Dev<T> D) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D.nc) return;
+  const int hb = D.ctl->hpar;
+  bool zero = true;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const T r = D.rDn[hb][D.coh[8 * c + p]];
+    D.rD[hb][(int64_t)p * D.nc + c] = r;
+    zero = zero && r == T(0);
+  }
+  D.cflag[hb][c] = zero ? 1 : 0;
+}
+
 // Kernel 5: the tail of a pass as its own small launch (kept out of the
 // gather, whose occupancy depends on a low register count).
 template <typename T>
@@ -507,8 +535,23 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
       return cudaGetLastError();
     }
   }
-  bool mixed = D.hex_variant >= kMixedVariant;
+  bool mixed = D.hex_variant >= kMixedVariant && D.ipair == nullptr;
   if constexpr (std::is_same<T, float>::value) mixed = mixed && D.sur_params == nullptr;
+  if (D.ipair != nullptr) {
+    // interfaces as node pairs: no interface kernel; the interface event
+    // pair is empty
+    if (ev) cudaEventRecord(ev[0], s);
+    launch_k(k_contact<T>, grid_of(D.ns, kActRun), kActRun, s, D);
+    if (ev) cudaEventRecord(ev[1], s);
+    launch_hex(D, M, s);
+    if (ev) cudaEventRecord(ev[2], s);
+    if (ev) cudaEventRecord(ev[3], s);
+    launch_k(k_gather_pairs<T>, grid_of(D.nn, gather_block), gather_block, s, D, M);
+    if (ev) cudaEventRecord(ev[4], s);
+    launch_k(k_tail<T>, 1, 256, s, D);
+    if (ev) cudaEventRecord(ev[5], s);
+    return cudaGetLastError();
+  }
   if (mixed) {
     // one launch for both element kinds; the interface event pair is empty
     if (ev) cudaEventRecord(ev[0], s);
@@ -546,8 +589,19 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
 }
 
 template <typename T>
+cudaError_t launch_pairs_to_elements(const Dev<T> &D, cudaStream_t s) {
+  if (D.ipair == nullptr || D.nc == 0) return cudaSuccess;
+  k_pairs_to_elements<T><<<grid_of(D.nc, 256), 256, 0, s>>>(D);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_damage_field(const Dev<T> &D, const Mat<T> &M, int which, float *out,
                                 cudaStream_t s) {
+  if (which == PDN_FIELD_DCOH) {
+    const cudaError_t e = launch_pairs_to_elements(D, s);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t n = (which == PDN_FIELD_DCOH) ? D.nc : D.nh;
   k_damage_field<T><<<grid_of(n, 128), 128, 0, s>>>(D, M, which, out);
   return cudaGetLastError();
@@ -562,6 +616,8 @@ template cudaError_t launch_pass<float>(const Dev<float> &, const Mat<float> &, 
                                         cudaEvent_t *, cudaStream_t, cudaEvent_t, cudaEvent_t);
 template cudaError_t launch_pass<double>(const Dev<double> &, const Mat<double> &, cudaStream_t, int32_t,
                                          cudaEvent_t *, cudaStream_t, cudaEvent_t, cudaEvent_t);
+template cudaError_t launch_pairs_to_elements<float>(const Dev<float> &, cudaStream_t);
+template cudaError_t launch_pairs_to_elements<double>(const Dev<double> &, cudaStream_t);
 template cudaError_t launch_damage_field<float>(const Dev<float> &, const Mat<float> &, int, float *,
                                                 cudaStream_t);
 template cudaError_t launch_damage_field<double>(const Dev<double> &, const Mat<double> &, int, float *,

@@ -72,7 +72,7 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(pkg.MeshDesc) == 4 * 8 + 5 * 8 + 8 + 2 * 8
     assert ctypes.sizeof(pkg.Material) == 31 * 8
     assert ctypes.sizeof(pkg.Options) == 4 * 4 + 3 * 8 + 3 * 8 + 8 + 8
-    assert ctypes.sizeof(pkg.Info) == 5 * 8 + 8 * 8 + 4 * 4 + 12 * 8
+    assert ctypes.sizeof(pkg.Info) == 5 * 8 + 8 * 8 + 6 * 4 + 12 * 8
     assert ctypes.sizeof(pkg.BatchInfo) == 10 * 4 + 4 * 8 + 2 * 8 + 16 * 8 + 3 * 16 * 4 + 2 * 4 + 16 * 4
     assert ctypes.sizeof(pkg.RefinedInfo) == 6 * 8 + 2 * 4 + 8
 

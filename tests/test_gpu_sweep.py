@@ -1,4 +1,4 @@
-"""The column sweep (pdn_info.sweep): one kernel evaluates the hexes and
+"""The column sweep (pdn_info.sweep, planned on request: PDN_SWEEP=1): one kernel evaluates the hexes and
 interfaces of a tile of element columns layer by layer and updates the nodes
 inside the tile from shared memory, in the gather's order; tile-boundary and
 chunk-boundary nodes go through the element-force slots and a gather over
@@ -118,10 +118,11 @@ def test_sweep_against_oracle_through_release(pkg, monkeypatch):
     o.close()
 
 
-def test_full_size_plates_plan_a_sweep(pkg):
-    """The 128x192x16 plate gets 8 x 4 tiles, the 400x600x32 plate 16 x 8
-    tiles (the first shape whose tiles give each of the 152 SMs eight
-    blocks)."""
+def test_full_size_plates_plan_a_sweep(pkg, monkeypatch):
+    """Asked for (PDN_SWEEP=1), the 128x192x16 plate gets 8 x 4 tiles, the
+    400x600x32 plate 16 x 8 tiles (the first shape whose tiles give each of
+    the 152 SMs eight blocks)."""
+    monkeypatch.setenv("PDN_SWEEP", "1")
     for w, tile in ((pi.damage_fp32_plate(), 3), (pi.large_fp32_plate(), 1)):
         c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP32_FORCE)
         info = pkg.pdn_get_info(c)
