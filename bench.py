@@ -129,6 +129,14 @@ def step_alg_bytes_state(n_hex, n_hex_hist, n_coh, n_coh_hist, n_nodes, n_surf) 
             + n_nodes * (12 + 12 + 12 + 48 + 48 + 8 + 1) + n_surf * 48)
 
 
+def kernels_per_pass(info: dict, n_coh: int) -> int:
+    """Kernels one pass launches: contact, hex, gather and tail, plus the
+    interface kernel where interface elements are evaluated on their own
+    (not as node pairs inside the gather, nor inside the mixed kernel)."""
+    separate_coh = n_coh > 0 and not info.get("coh_pairs", 0) and info["hex_variant"] < 4
+    return 5 if separate_coh else 4
+
+
 def issue_bound_ms(warp_instructions: float, sm_mhz: float, n_sm: int = 152) -> float:
     """Time to issue a launch's warp instructions at one instruction per
     cycle on each of the four schedulers of every SM."""
@@ -482,9 +490,7 @@ def run_gpu(args, ws, rank, local):
     info = pkg.pdn_get_info(ctx)
     repeats = info["n_repeats"] - rep0
     ms = max_over_ranks(dist, [ms], "cuda")[0]
-    mixed = info["hex_variant"] >= 4  # one kernel for hexes and interface elements
-    kernels_per_pass = 5 if (plate.n_coh > 0 and not mixed) else 4  # contact, hex, [coh], gather, tail
-    gpu_launches = (K + repeats) * kernels_per_pass + 1  # + the target/mode kernel of the call
+    gpu_launches = (K + repeats) * kernels_per_pass(info, plate.n_coh) + 1  # + the target/mode kernel
     value = whole_job_rate(ws, plate.n_hex * K, ms)
     fh = pkg.pdn_contact_force(ctx)[2]
     f_window = fh[len(f_before):]
@@ -540,7 +546,8 @@ def run_gpu(args, ws, rank, local):
         "roofline": roofline,
         "kernel_ms": {k: v[0] for k, v in prof.items()},
         "kernel_launches": {k: v[1] for k, v in prof.items()}, "profile_steps": args.profile_steps,
-        "autotune": {"element_variant": info["hex_variant"], "force_pass_ms_per_variant": info["tune_ms"]},
+        "autotune": {"element_variant": info["hex_variant"], "force_pass_ms_per_variant": info["tune_ms"],
+                     "interfaces": ("node pairs in the gather" if info["coh_pairs"] else "interface elements")},
         "gpu_launches": gpu_launches,
         "clocks": clock_summary,
     }
@@ -802,7 +809,7 @@ def run_mmu(args, ws, rank, local):
         "kernel_ms": {k: v[0] for k, v in prof.items()},
         "e2e": {"value": whole_job_rate(ws, nh1 * K, t_e2e * 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K, "seconds": t_e2e},
-        "gpu_launches": (K + repeats) * 5 + 1,
+        "gpu_launches": (K + repeats) * kernels_per_pass(info, nc1) + 1,
         "clocks": clocks.summary(),
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

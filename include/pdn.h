@@ -179,14 +179,18 @@ typedef struct {
                               and kept by the first pdn_step while PDN_SWEEP=1 is still
                               set; a planned sweep keeps the interface elements
                               (coh_pairs 0) */
-  int32_t coh_pairs;       /* 1: interfaces evaluated as node pairs inside the gather (flat
+  int32_t coh_pairs;       /* 1, 2: interfaces evaluated as node pairs inside the gather (flat
                               interfaces, at most eight elements per node, no column sweep):
                               with Newton-Cotes points at the corners (Sec. 2.3.2) the
                               traction at a point depends only on the jump of the two
                               coincident nodes there, so the law is evaluated once per node
                               and each incident element's share added in CSR order, with
                               the same sums as the interface kernel; no interface kernel
-                              runs.  0: interface elements (k_coh).  The environment
+                              runs; 2 where the node numbering is layered (blocks of
+                              consecutive ids are node layers and a node's partner is the
+                              same position in the next layer), so that the gather finds
+                              the partner from the node id, 1 otherwise (a partner table).
+                              0: interface elements (k_coh).  The environment
                               variable PDN_COH_PAIRS=0, read by pdn_init_mesh, keeps the
                               interface elements */
   int32_t reserved;

@@ -665,6 +665,8 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // incident interface element of a node.  PDN_COH_PAIRS=0, read here, keeps
   // the interface elements.
   bool pairs_on = false, pairs_uniform = true;
+  int32_t pair_layer = 0;
+  uint64_t pair_mask[2][2] = {{0, 0}, {0, 0}};
   std::vector<int2> ipair;
   std::vector<char> iw;  // [nn] 4 weights of the element precision
   double coh_w = 0.0;
@@ -723,6 +725,29 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     };
     if (allowed && nc > 0 && all_flat_coh && ell && !sweep_on)
       pairs_on = opt->precision == PDN_FP64 ? build_pairs(double{}) : build_pairs(float{});
+    // a layered numbering: blocks of L consecutive ids are node layers, and
+    // every interface node's partner is the same position one layer up (lower
+    // side) or down (upper side), with at most four hexes per interface node
+    if (pairs_on) {
+      int64_t L = 0;
+      for (int64_t j = 0; j < nn && L == 0; ++j)
+        if (ipair[j].x >= 0) L = std::llabs((int64_t)ipair[j].x - j);
+      bool ok = L > 0 && nn % L == 0 && nn / L <= kMaxPairLayers;
+      for (int64_t l = 0; ok && l < nn / L; ++l) {
+        const int64_t j0 = l * L;
+        const int kind = ipair[j0].x < 0 ? 0 : (((ipair[j0].y >> 3) & 1) ? 2 : 1);
+        for (int64_t j = j0; ok && j < j0 + L; ++j) {
+          const int2 ip = ipair[j];
+          if (kind == 0)
+            ok = ip.x < 0;
+          else
+            ok = ip.x == (kind == 1 ? j + L : j - L) && ((ip.y >> 3) & 1) == (kind == 2 ? 1 : 0) &&
+                 ((ip.y >> 4) & 15) <= 4;
+        }
+        if (ok && kind) pair_mask[kind - 1][l >> 6] |= uint64_t(1) << (l & 63);
+      }
+      if (ok) pair_layer = (int32_t)L;
+    }
     if (!pairs_on) {
       std::vector<int2>().swap(ipair);
       std::vector<char>().swap(iw);
@@ -886,6 +911,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   for (int64_t j = 0; j < nn; ++j) {
     nflag[j] = mesh->fixed ? mesh->fixed[j] : 0;
     if (surf_of[j] >= 0) nflag[j] |= 8;
+    if (pairs_on && ipair[j].x >= 0) nflag[j] |= (uint8_t)((ipair[j].y & 7) << kFlagPairShift);
   }
   std::vector<double> Xs(3 * std::max<int64_t>(ns, 1), 0.0);
   for (int64_t s = 0; s < ns; ++s)
@@ -1022,6 +1048,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     D.iw = (pairs_on && !pairs_uniform) ? reinterpret_cast<const V4 *>(P.iw) : nullptr;
     D.coh_w = (T)coh_w;
     for (int b = 0; b < 2; ++b) D.rDn[b] = pairs_on ? reinterpret_cast<T *>(P.rDn[b]) : nullptr;
+    D.pair_layer = pair_layer;
+    for (int k = 0; k < 2; ++k)
+      for (int w = 0; w < 2; ++w) D.pair_mask[k][w] = pair_mask[k][w];
     D.nrm = d_nrm;
     D.lam = d_lam;
     D.trial = d_trial;
@@ -1491,7 +1520,12 @@ int pdn_get_info(pdn_ctx *ctx, pdn_info *info) {
   info->precision = ctx->precision;
   info->hex_variant = ctx->precision == PDN_FP64 ? ctx->Dd.hex_variant : ctx->Df.hex_variant;
   info->sweep = (ctx->precision == PDN_FP32_FORCE && ctx->Df.sweep != nullptr) ? 1 + ctx->sweep.tile : 0;
-  info->coh_pairs = (ctx->precision == PDN_FP64 ? ctx->Dd.ipair : ctx->Df.ipair) != nullptr ? 1 : 0;
+  {
+    const bool f64 = ctx->precision == PDN_FP64;
+    const bool pairs = (f64 ? ctx->Dd.ipair : ctx->Df.ipair) != nullptr;
+    const bool layered = (f64 ? ctx->Dd.pair_layer : ctx->Df.pair_layer) > 0;
+    info->coh_pairs = pairs ? (layered ? 2 : 1) : 0;
+  }
   info->reserved = 0;
   for (int v = 0; v < 12; ++v) info->tune_ms[v] = ctx->tune_ms[v];
   return PDN_OK;

@@ -778,6 +778,8 @@ static int pdn_batch_init_body(pdn_batch **out, int32_t n_plates, const pdn_mesh
     // their thresholds in the element layout (no node pairs)
     b->plates[p]->Df.ipair = nullptr;
     b->plates[p]->Dd.ipair = nullptr;
+    b->plates[p]->Df.pair_layer = 0;
+    b->plates[p]->Dd.pair_layer = 0;
   }
   int rc = b->precision == PDN_FP64 ? upload_records<double>(b) : upload_records<float>(b);
   if (rc) return fail_init(rc, b->err);

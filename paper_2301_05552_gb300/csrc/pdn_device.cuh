@@ -23,6 +23,20 @@ __device__ __forceinline__ float xpow(float x, float y) { return powf(x, y); }
 __device__ __forceinline__ double xpow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ bool xfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool xfinite(float x) { return isfinite(x); }
+// Operations rounded one at a time, which no multiply-add contraction may
+// merge: code evaluated in several kernels (the cohesive law: the interface
+// kernel, the node-pair gather, the sweep, the batched kernel) then rounds
+// identically in all of them.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rsqrt_rn(float a) { return __fsqrt_rn(a); }
+__device__ __forceinline__ double rsqrt_rn(double a) { return __dsqrt_rn(a); }
 
 // Exact float <-> double conversions with integer instructions.  On this part
 // the hardware conversions issue at the FP64 rate (about 0.6 T/s, measured),
@@ -190,6 +204,27 @@ __device__ __forceinline__ void repeat_mark_nodes(uint8_t *mark, const int nd[8]
   if (mark == nullptr) return;
 #pragma unroll
   for (int a = 0; a < 8; ++a) mark[nd[a]] = 1;
+}
+
+// ---------------------------------------------------------------------------
+// Slots of an element's eight nodal forces.  With eight slots per node
+// (D.rank set) slot = 8 node + rank, the node ids re-read from the
+// connectivity (still in L1 from the element's start) and the ranks packed
+// 3 bits per corner; otherwise the precomputed positions.
+template <typename T>
+__device__ __forceinline__ void element_slots(const Dev<T> &D, const int32_t *conn, int64_t e, const int4 *pos2,
+                                              uint32_t rk, int (&ps)[8]) {
+  if (D.rank != nullptr) {
+    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e);
+    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e + 1);
+    const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) ps[a] = 8 * nd[a] + (int)((rk >> (3 * a)) & 7u);
+  } else {
+    const int4 p0 = __ldg(pos2), p1 = __ldg(pos2 + 1);
+    ps[0] = p0.x, ps[1] = p0.y, ps[2] = p0.z, ps[3] = p0.w;
+    ps[4] = p1.x, ps[5] = p1.y, ps[6] = p1.z, ps[7] = p1.w;
+  }
 }
 
 // PDN_CHECK builds: the eight node ids of an element lie in [0, n_nodes);
@@ -408,27 +443,31 @@ __device__ __forceinline__ void cdm_damage(const Mat<T> &M, const ElemLaw<T> &L,
 // (1, 2 tangential, 3 normal).  Same reading as the oracle.
 template <typename T>
 __device__ __forceinline__ void czm(const Mat<T> &M, const T (&dl)[3], T rin, T &rout, T (&tau)[3]) {
-  const T dsh2 = dl[0] * dl[0] + dl[1] * dl[1];
+  // every product, sum and quotient rounded on its own (rmul, radd, ...),
+  // in the order written
+  const T dsh2 = radd(rmul(dl[0], dl[0]), rmul(dl[1], dl[1]));
   const T d3p = dl[2] > T(0) ? dl[2] : T(0);
-  const T en = M.KI * d3p * d3p + M.Ksh * dsh2;  // K_B lambda^2
+  const T kd3 = rmul(rmul(M.KI, d3p), d3p), ksh = rmul(M.Ksh, dsh2);
+  const T en = radd(kd3, ksh);  // K_B lambda^2
   T D = T(0);
   T r = rin;
   if (rin > T(0) || en >= M.onset_floor) {
-    const T den = M.Ksh * dsh2 + M.KI * d3p * d3p;
-    const T B = den > T(0) ? M.Ksh * dsh2 / den : T(0);
-    const T KB = (T(1) - B) * M.KI + B * M.Ksh;
-    const T lam = xsqrt(en / KB);
+    const T B = en > T(0) ? rdiv(ksh, en) : T(0);
+    const T KB = radd(rmul(rsub(T(1), B), M.KI), rmul(B, M.Ksh));
+    const T lam = rsqrt_rn(rdiv(en, KB));
     const T Beta = xpow(B, M.eta);
-    const T lo = xsqrt((M.KI_D3o2 + (M.Ksh_Dsho2 - M.KI_D3o2) * Beta) / KB);
-    const T lcr = (M.KI_D3oD3c + (M.Ksh_DshoDshc - M.KI_D3oD3c) * Beta) / (KB * lo);
-    T H = (lam - lo) / (lcr - lo);
+    const T lo = rsqrt_rn(rdiv(radd(M.KI_D3o2, rmul(rsub(M.Ksh_Dsho2, M.KI_D3o2), Beta)), KB));
+    const T lcr = rdiv(radd(M.KI_D3oD3c, rmul(rsub(M.Ksh_DshoDshc, M.KI_D3oD3c), Beta)), rmul(KB, lo));
+    T H = rdiv(rsub(lam, lo), rsub(lcr, lo));
     H = H < T(0) ? T(0) : (H > T(1) ? T(1) : H);
     r = rin > H ? rin : H;
-    D = r * lcr / (r * lcr + (T(1) - r) * lo);
+    const T rl = rmul(r, lcr);
+    D = rdiv(rl, radd(rl, rmul(rsub(T(1), r), lo)));
   }
-  tau[0] = (T(1) - D) * M.Ksh * dl[0];
-  tau[1] = (T(1) - D) * M.Ksh * dl[1];
-  tau[2] = (dl[2] >= T(0)) ? (T(1) - D) * M.KI * dl[2] : M.KI * dl[2];
+  const T s = rsub(T(1), D);
+  tau[0] = rmul(rmul(s, M.Ksh), dl[0]);
+  tau[1] = rmul(rmul(s, M.Ksh), dl[1]);
+  tau[2] = (dl[2] >= T(0)) ? rmul(rmul(s, M.KI), dl[2]) : rmul(M.KI, dl[2]);
   rout = r;
 }
 

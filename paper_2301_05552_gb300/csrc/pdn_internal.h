@@ -245,7 +245,18 @@ struct Dev {
   // double-buffered with the history); the element layout rD/cflag is
   // written from it only for the readers (history, energy, damage field)
   T *rDn[2];
+  // Node pairs of a layered numbering (every block of pair_layer consecutive
+  // node ids is one node layer, and the partner of an interface node is the
+  // same position in the layer above or below): the gather then knows a
+  // node's partner from its id and loads everything in one round.  Bit l of
+  // pair_mask[0] / pair_mask[1] (words of 64 layers): layer l is the lower /
+  // upper side of an interface; node flag bits 4-6 hold the count of a node's
+  // interface elements.  0: partners from ipair (a second load round).
+  int32_t pair_layer;
+  uint64_t pair_mask[2][2];
 };
+constexpr int kMaxPairLayers = 128;
+constexpr int kFlagPairShift = 4;  // node flag bits 4-6: incident interface elements
 
 // Launchers (pdn_kernels.cu).
 template <typename T>

@@ -30,27 +30,6 @@ namespace pdn {
 namespace detail {
 
 // ---------------------------------------------------------------------------
-// Slots of an element's eight nodal forces.  With eight slots per node
-// (D.rank set) slot = 8 node + rank, the node ids re-read from the
-// connectivity (still in L1 from the element's start) and the ranks packed
-// 3 bits per corner; otherwise the precomputed positions.
-template <typename T>
-__device__ __forceinline__ void element_slots(const Dev<T> &D, const int32_t *conn, int64_t e, const int4 *pos2,
-                                              uint32_t rk, int (&ps)[8]) {
-  if (D.rank != nullptr) {
-    const int4 c0 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e);
-    const int4 c1 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e + 1);
-    const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-#pragma unroll
-    for (int a = 0; a < 8; ++a) ps[a] = 8 * nd[a] + (int)((rk >> (3 * a)) & 7u);
-  } else {
-    const int4 p0 = __ldg(pos2), p1 = __ldg(pos2 + 1);
-    ps[0] = p0.x, ps[1] = p0.y, ps[2] = p0.z, ps[3] = p0.w;
-    ps[4] = p1.x, ps[5] = p1.y, ps[6] = p1.z, ps[7] = p1.w;
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Kernel 1: contact detection and projection (Sec. 2.1, Fig. 1, Algorithm 1).
 // One thread per contact-surface node.  The striker state of the step being
 // computed (its RK4 update with the committed contact force held over the
@@ -765,7 +744,7 @@ __device__ __forceinline__ bool coh_forces(const Dev<T> &D, const Mat<T> &M, int
       rv[p] = r1;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const T tg = w * tau[i];
+        const T tg = rmul(w, tau[i]);  // rounded alone, as in the node-pair gather
         f[p + 4][i] = tg;
         f[p][i] = -tg;
       }
@@ -1342,23 +1321,80 @@ __device__ __forceinline__ void gather_item(const Dev<T> &D, int64_t j, int mode
   node_update(D, j, mode, q, fx, fy, fz);
 }
 
-// Products that no multiply-add contraction may absorb: the interface
-// shares below must round exactly as the stored slots of the element path.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-
-// The gather of one node when interfaces are node pairs (Dev::ipair).  The
-// node's hex slots come in the first load round with its state (the first
-// four always, the rest when it has more hexes); an interface node then reads
-// its own and its partner's displacement mirror and the pair's threshold,
-// evaluates the cohesive law (Algorithm 5) once for the Newton-Cotes point
-// that the pair forms in each incident interface element (Sec. 2.3.2), and
-// adds each element's share w tau (upper node) or -w tau (lower node) in CSR
+// The interface part of a node's force when interfaces are node pairs: the
+// cohesive law (Algorithm 5) evaluated once for the Newton-Cotes point that
+// the pair forms in each incident interface element (Sec. 2.3.2), from the
+// jump upper minus lower and the pair's committed threshold rin, and each
+// element's share w tau (upper node) or -w tau (lower node) added in CSR
 // order: the sums of the interface kernel's slots, in the same order and
 // rounding.  The lower node writes the pair's new threshold; an undamaged
 // pair (r_D = 0 before and after) in a new step writes nothing, since the
 // other buffer then holds 0 as well (r_D never decreases, and only the
 // passes of the step write it).
+template <typename T>
+__device__ __forceinline__ void pair_forces(const Dev<T> &D, const Mat<T> &M, int64_t j, int mode, bool top,
+                                            const T (&us)[3], const T (&up)[3], T rin, int kc, const T (&w)[4],
+                                            T &fx, T &fy, T &fz) {
+  const T dl[3] = {top ? us[0] - up[0] : up[0] - us[0], top ? us[1] - up[1] : up[1] - us[1],
+                   top ? us[2] - up[2] : up[2] - us[2]};
+  T tau[3], r1;
+  czm(M, dl, rin, r1, tau);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (k < kc) {
+      const T tx = rmul(w[k], tau[0]), ty = rmul(w[k], tau[1]), tz = rmul(w[k], tau[2]);
+      if (top) {
+        fx += tx;
+        fy += ty;
+        fz += tz;
+      } else {
+        fx -= tx;
+        fy -= ty;
+        fz -= tz;
+      }
+    }
+  if (!top && (mode == MODE_REPEAT || (mode == MODE_ADVANCE && (rin != T(0) || r1 != T(0)))))
+    D.rDn[D.ctl->hpar ^ 1][j] = r1;
+}
+
+template <typename T>
+__device__ __forceinline__ void pair_weights(const Dev<T> &D, int64_t j, T (&w)[4]) {
+  using V4 = typename Vec4T<T>::type;
+  if (D.iw != nullptr) {
+    const V4 wv = D.iw[j];
+    w[0] = wv.x;
+    w[1] = wv.y;
+    w[2] = wv.z;
+    w[3] = wv.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w[k] = D.coh_w;
+  }
+}
+
+// The node's own displacement mirror: in the stepping passes it is the
+// element-precision rounding of the committed FP64 displacement already
+// loaded (the mirror is always written as that rounding), so it is not read
+// again; an internal-force pass reads it.
+template <typename T>
+__device__ __forceinline__ void own_mirror(const Dev<T> &D, int64_t j, int mode, int ub, const NodeState<T> &q,
+                                           T (&us)[3]) {
+  if (mode == MODE_FORCES) {
+    const auto u = D.u4[ub][j];
+    us[0] = u.x;
+    us[1] = u.y;
+    us[2] = u.z;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) us[i] = to_elem(q.dc[i], T(0));
+  }
+}
+
+// The gather of one node when interfaces are node pairs with partners from
+// Dev::ipair: the node's hex slots come in the first load round with its
+// state (the first four always, the rest when it has more hexes); an
+// interface node then reads its partner's displacement mirror and the pair's
+// threshold (a second round) and adds the interface part (pair_forces).
 template <typename T>
 __device__ __forceinline__ void gather_pair_item(const Dev<T> &D, const Mat<T> &M, int64_t j, int mode) {
   using V4 = typename Vec4T<T>::type;
@@ -1386,43 +1422,76 @@ __device__ __forceinline__ void gather_pair_item(const Dev<T> &D, const Mat<T> &
   if (ip.x >= 0) {
     const Ctl *ctl = D.ctl;
     const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
-    const int hb = ctl->hpar;
     const bool top = (ip.y >> 3) & 1;
-    const int64_t lo = top ? (int64_t)ip.x : j;
-    const V4 us = D.u4[ub][j], up = D.u4[ub][ip.x];
-    const T rin = D.rDn[hb][lo];
-    T w[4];
-    if (D.iw != nullptr) {
-      const V4 wv = D.iw[j];
-      w[0] = wv.x;
-      w[1] = wv.y;
-      w[2] = wv.z;
-      w[3] = wv.w;
-    } else {
+    const V4 u = D.u4[ub][ip.x];
+    const T up[3] = {u.x, u.y, u.z};
+    const T rin = D.rDn[ctl->hpar][top ? (int64_t)ip.x : j];
+    T w[4], us[3];
+    pair_weights(D, j, w);
+    own_mirror(D, j, mode, ub, q, us);
+    pair_forces(D, M, j, mode, top, us, up, rin, ip.y & 7, w, fx, fy, fz);
+  }
+  node_update(D, j, mode, q, fx, fy, fz);
+}
+
+// The same for a layered numbering (Dev::pair_layer): the node's layer, and
+// with it whether it has a partner and which, follows from its id, so its
+// partner's mirror and the pair's threshold load in the same round as its
+// state and slots.  An interface node has at most four hexes, all on one
+// side; its other four slots belong to interface elements, which write no
+// slots here, so the first four slots hold its hex forces followed by zeros.
+template <typename T>
+__device__ __forceinline__ void gather_pair_layered_item(const Dev<T> &D, const Mat<T> &M, int64_t j, int mode) {
+  using V4 = typename Vec4T<T>::type;
+  if (j >= D.nn) return;
+  if (mode == MODE_REPEAT && !repeat_take(D.rmark_n, j)) return;
+  const Ctl *ctl = D.ctl;
+  const int ub = (mode == MODE_FORCES) ? (ctl->dpar ^ 1) : ctl->dpar;
+  const uint32_t L = (uint32_t)D.pair_layer;
+  const uint32_t lay = (uint32_t)j / L;
+  const int wd = lay >> 6, bit = lay & 63;
+  const bool lower = (((wd ? D.pair_mask[0][1] : D.pair_mask[0][0]) >> bit) & 1) != 0;
+  const bool upper = (((wd ? D.pair_mask[1][1] : D.pair_mask[1][0]) >> bit) & 1) != 0;
+  const bool pair = lower || upper;
+  NodeState<T> q;
+  node_state_load(D, j, mode, q);
+  const uint8_t fl = D.nflag[j];
+  const int64_t pj = upper ? j - (int64_t)L : j + (int64_t)L;
+  const V4 *fs = D.fe + 8 * j;
+  V4 f[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) w[k] = D.coh_w;
+  for (int k = 0; k < 4; ++k) f[k] = fs[k];
+  if (!pair) {
+#pragma unroll
+    for (int k = 4; k < 8; ++k) f[k] = fs[k];
+  }
+  V4 u;
+  T rin = T(0);
+  if (pair) {
+    u = D.u4[ub][pj];
+    rin = D.rDn[ctl->hpar][upper ? pj : j];
+  }
+  T w[4];
+  if (pair) pair_weights(D, j, w);
+  T fx = T(0), fy = T(0), fz = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    fx += f[k].x;
+    fy += f[k].y;
+    fz += f[k].z;
+  }
+  if (!pair) {
+#pragma unroll
+    for (int k = 4; k < 8; ++k) {
+      fx += f[k].x;
+      fy += f[k].y;
+      fz += f[k].z;
     }
-    const V4 ut = top ? us : up, ul = top ? up : us;
-    const T dl[3] = {ut.x - ul.x, ut.y - ul.y, ut.z - ul.z};
-    T tau[3], r1;
-    czm(M, dl, rin, r1, tau);
-    const int kc = ip.y & 7;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k < kc) {
-        const T tx = mul_rn(w[k], tau[0]), ty = mul_rn(w[k], tau[1]), tz = mul_rn(w[k], tau[2]);
-        if (top) {
-          fx += tx;
-          fy += ty;
-          fz += tz;
-        } else {
-          fx -= tx;
-          fy -= ty;
-          fz -= tz;
-        }
-      }
-    if (!top && (mode == MODE_REPEAT || (mode == MODE_ADVANCE && (rin != T(0) || r1 != T(0)))))
-      D.rDn[hb ^ 1][j] = r1;
+  } else {
+    const T up[3] = {u.x, u.y, u.z};
+    T us[3];
+    own_mirror(D, j, mode, ub, q, us);
+    pair_forces(D, M, j, mode, upper, us, up, rin, (fl >> kFlagPairShift) & 7, w, fx, fy, fz);
   }
   node_update(D, j, mode, q, fx, fy, fz);
 }

@@ -103,12 +103,22 @@ __global__ void __launch_bounds__(256) k_gather(Dev<T> D) {
 
 // Kernel 4 with interfaces as node pairs: the gather also evaluates the
 // cohesive law of each interface node pair (no interface kernel runs).
+// (FP32: at most 64 registers, four blocks of 256 per SM for this
+// memory-bound kernel)
 template <typename T>
-__global__ void __launch_bounds__(256) k_gather_pairs(Dev<T> D, Mat<T> M) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_pairs(Dev<T> D, Mat<T> M) {
   pdl_enter();
   const int mode = D.ctl->mode;
   if (mode >= MODE_DONE) return;
   gather_pair_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_gather_pairs_layered(Dev<T> D, Mat<T> M) {
+  pdl_enter();
+  const int mode = D.ctl->mode;
+  if (mode >= MODE_DONE) return;
+  gather_pair_layered_item(D, M, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, mode);
 }
 
 // The element layout of the interface thresholds (rD, cflag at the
@@ -546,7 +556,10 @@ cudaError_t launch_pass(const Dev<T> &D, const Mat<T> &M, cudaStream_t s, int32_
     launch_hex(D, M, s);
     if (ev) cudaEventRecord(ev[2], s);
     if (ev) cudaEventRecord(ev[3], s);
-    launch_k(k_gather_pairs<T>, grid_of(D.nn, gather_block), gather_block, s, D, M);
+    if (D.pair_layer > 0)
+      launch_k(k_gather_pairs_layered<T>, grid_of(D.nn, gather_block), gather_block, s, D, M);
+    else
+      launch_k(k_gather_pairs<T>, grid_of(D.nn, gather_block), gather_block, s, D, M);
     if (ev) cudaEventRecord(ev[4], s);
     launch_k(k_tail<T>, 1, 256, s, D);
     if (ev) cudaEventRecord(ev[5], s);

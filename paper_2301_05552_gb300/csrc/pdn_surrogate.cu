@@ -603,9 +603,9 @@ __global__ void __launch_bounds__(kHexSurBlock, 3) k_hex_sur(Dev<float> D, Mat<f
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][el] = (pristine_in && !dirty) ? 1 : 0;
   float f[8][3];
   from_modes(C, f);
-  const int4 p0 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * el);
-  const int4 p1 = __ldg(reinterpret_cast<const int4 *>(D.pos) + 2 * el + 1);
-  const int ps[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+  int ps[8];
+  element_slots(D, D.hex, el, reinterpret_cast<const int4 *>(D.pos) + 2 * el,
+                D.rank != nullptr ? __ldg(D.rank + el) : 0u, ps);
 #pragma unroll
   for (int a = 0; a < 8; ++a) D.fe[ps[a]] = make_float4(f[a][0], f[a][1], f[a][2], 0.0f);
 }

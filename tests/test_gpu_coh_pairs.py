@@ -11,8 +11,9 @@ force slots; element variant 0 on both sides): the same states, contact
 force histories, history buffers, energies and interface damage fields, bit
 for bit, on seeded damaging states (FP32 and FP64), through an impact with
 node release and repetition (Algorithm 2), on the cut-down AS4 coupon with
-frame, clamps and gravity, and on a plate whose element sizes vary (area
-weights per node instead of one weight).  The products w tau are rounded
+frame, clamps and gravity, on a plate whose element sizes vary (area
+weights per node instead of one weight), and on plates whose node ids are
+permuted (partners from the pair table instead of the layered numbering).  The products w tau are rounded
 alone on both sides, so the sums agree to the bit unless the compiler
 contracts the law's own products differently in the two kernels; the test
 prints which and bounds the difference at FP32 rounding."""
@@ -51,6 +52,20 @@ def _graded_plate():
     return w
 
 
+def _renumbered(w, seed=3):
+    """The same plate with its node ids permuted at random: interfaces stay
+    flat, but the numbering is no longer layered (partners from a table)."""
+    import dataclasses
+    P = w.plate
+    perm = np.random.default_rng(seed).permutation(P.n_nodes)  # new id of old node i
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(P.n_nodes)
+    plate = dataclasses.replace(P, X=np.ascontiguousarray(P.X[:, inv]), hex=perm[P.hex].astype(np.int32),
+                                coh=perm[P.coh].astype(np.int32), fixed=np.ascontiguousarray(P.fixed[inv]),
+                                surf=np.sort(perm[P.surf]).astype(np.int32))
+    return dataclasses.replace(w, plate=plate)
+
+
 def _cases():
     out = []
     w = pi.damage_fp32_plate(nx=32, ny=48, plies=8, Lx=12.5, Ly=18.75, H=2.2, steps=120)
@@ -62,6 +77,11 @@ def _cases():
     out.append(("impact_release_20x13x8", w, False))
     out.append(("as4_cut_down_40x28x8_fp32", pi.reduced_as4_frame_plate(fp64=False, steps=2000), False))
     out.append(("graded_24x32x8", _graded_plate(), True))
+    w = pi.damage_fp32_plate(nx=20, ny=13, plies=4, elems_per_ply=2, Lx=10.0, Ly=6.5, H=1.1,
+                             mass=5.5e-3 / 2048, speed=20000.0, steps=3000)
+    out.append(("renumbered_impact_20x13x8", _renumbered(w), False))
+    w = pi.damage_fp32_plate(nx=16, ny=24, plies=8, Lx=12.5, Ly=18.75, H=2.2, steps=60)
+    out.append(("renumbered_seeded_16x24x8", _renumbered(w), True))
     return out
 
 
@@ -81,7 +101,8 @@ def _rel(a, b):
 def test_pairs_equal_interface_elements(pkg, monkeypatch, name, w, seeded):
     a = _solver(pkg, w, True, monkeypatch)
     b = _solver(pkg, w, False, monkeypatch)
-    assert pkg.pdn_get_info(a.ctx)["coh_pairs"] == 1
+    # layered numbering (partner from the node id) unless renumbered
+    assert pkg.pdn_get_info(a.ctx)["coh_pairs"] == (1 if name.startswith("renumbered") else 2)
     assert pkg.pdn_get_info(b.ctx)["coh_pairs"] == 0
     if seeded:
         _seed(pkg, w, a, b)
@@ -104,7 +125,7 @@ def test_pairs_equal_interface_elements(pkg, monkeypatch, name, w, seeded):
           f"peak {fb.max() if fb.size else 0.0:.3f} N, repeats {na}/{nb}")
     if seeded:
         assert (rb > 0).any(), "case must damage interfaces"
-    if name.startswith("impact"):
+    if "impact" in name:
         assert nb > 0, "case must release nodes"
     assert na == nb
     assert _rel(da, db) <= 1e-6 and _rel(va, vb) <= 1e-4
@@ -143,7 +164,7 @@ def test_pairs_are_the_default_where_the_mesh_allows(pkg, monkeypatch):
     w = pi.damage_fp32_plate()
     c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP32_FORCE)
     info = pkg.pdn_get_info(c)
-    assert info["coh_pairs"] == 1 and info["sweep"] == 0
+    assert info["coh_pairs"] == 2 and info["sweep"] == 0
     c.close()
     w = pi.plain_fp64_plate(nx=8, ny=8)
     c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP64)
@@ -158,3 +179,4 @@ def test_pairs_are_the_default_where_the_mesh_allows(pkg, monkeypatch):
     c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP32_FORCE)
     assert pkg.pdn_get_info(c)["coh_pairs"] == 0
     c.close()
+
