@@ -490,6 +490,8 @@ def run_gpu(args, ws, rank, local):
     info = pkg.pdn_get_info(ctx)
     repeats = info["n_repeats"] - rep0
     ms = max_over_ranks(dist, [ms], "cuda")[0]
+    # one kernel for hexes and interface elements (never with node pairs)
+    mixed = info["hex_variant"] >= 4 and not info["coh_pairs"]
     gpu_launches = (K + repeats) * kernels_per_pass(info, plate.n_coh) + 1  # + the target/mode kernel
     value = whole_job_rate(ws, plate.n_hex * K, ms)
     fh = pkg.pdn_contact_force(ctx)[2]

@@ -111,3 +111,42 @@ def test_traffic_record_hash_covers_the_hex_kernel_only():
     for name in ("contact_item", "coh_item", "tail_block", "gather_item"):
         assert name in text and name not in kept
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_bench_functions_use_only_defined_names():
+    """Every name a function of bench.py reads is a parameter, a local, a
+    module-level name or a builtin (the GPU legs cannot run here, so a name
+    left behind by an edit would otherwise surface only on the GPU)."""
+    import ast
+    import builtins
+
+    src = open(os.path.join(ROOT, "bench.py"), encoding="utf-8").read()
+    tree = ast.parse(src)
+    module = set()
+    for n in tree.body:
+        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            module.add(n.name)
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            module.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, (ast.Assign, ast.AnnAssign)):
+            for t in (n.targets if isinstance(n, ast.Assign) else [n.target]):
+                module.update(m.id for m in ast.walk(t) if isinstance(m, ast.Name))
+    missing = []
+    for fn in [n for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)]:
+        local = set()
+        for n in ast.walk(fn):
+            if isinstance(n, ast.arg):
+                local.add(n.arg)
+            elif isinstance(n, ast.Name) and isinstance(n.ctx, (ast.Store, ast.Del)):
+                local.add(n.id)
+            elif isinstance(n, ast.FunctionDef):
+                local.add(n.name)
+            elif isinstance(n, (ast.Import, ast.ImportFrom)):
+                local.update((a.asname or a.name).split(".")[0] for a in n.names)
+            elif isinstance(n, ast.ExceptHandler) and n.name:
+                local.add(n.name)
+        for n in ast.walk(fn):
+            if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load):
+                if n.id not in local and n.id not in module and not hasattr(builtins, n.id):
+                    missing.append(f"{fn.name}:{n.lineno}:{n.id}")
+    assert not missing, missing
