@@ -33,6 +33,19 @@ namespace {
 using namespace detail;
 
 enum TileKind : int32_t { TK_CONTACT = 0, TK_HEX = 1, TK_COH = 2, TK_GATHER = 3, TK_TAIL = 4 };
+
+// The gather of one node of a plate: with the plate's interfaces as node
+// pairs (Dev::ipair) the gather evaluates them too, and the plate has no
+// interface tiles.
+template <typename T>
+__device__ __forceinline__ void batch_gather(const Dev<T> &D, const Mat<T> &M, int64_t i, int mode) {
+  if (D.ipair == nullptr)
+    gather_item(D, i, mode);
+  else if (D.pair_layer > 0)
+    gather_pair_layered_item(D, M, i, mode);
+  else
+    gather_pair_item(D, M, i, mode);
+}
 constexpr int kPhases = 4;          // contact, elements (hex + interface), gather, tails
 constexpr int kBatchBlock = 128;    // threads per block (the hex register budget is set for 128)
 constexpr int kBatchPasses = 32;    // passes per persistent launch (it stops early when all plates are done)
@@ -170,7 +183,7 @@ __global__ void __launch_bounds__(kBatchBlock, MINB) k_batch(BatchArgs<T> A) {
             break;
           case TK_GATHER:
             if (mode < MODE_DONE)
-              for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) gather_item(sD, i, mode);
+              for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) batch_gather(sD, sM, i, mode);
             break;
           default:  // TK_TAIL
             if (mode < MODE_DONE) {
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(kBatchBlock, MINB) k_batch_flow(FlowArgs<T> A)
         break;
       case TK_GATHER:
         if (mode < MODE_DONE)
-          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) gather_item(sD, i, mode);
+          for (int64_t i = tl.z + threadIdx.x; i < tl.w; i += blockDim.x) batch_gather(sD, sM, i, mode);
         break;
       default:  // TK_TAIL
         if (mode < MODE_DONE) {
@@ -422,6 +435,14 @@ const void *kernel_ptr(const pdn_batch *b, int flow, int var) {
   return b->precision == PDN_FP64 ? kernel_for<double>(flow, var) : kernel_for<float>(flow, var);
 }
 
+// Interface elements a plate's element phase evaluates: none when its
+// interfaces are node pairs (the gather evaluates them).
+int64_t coh_items(const pdn_batch *b, int p) {
+  const pdn_ctx *c = b->plates[p];
+  const bool pairs = (b->precision == PDN_FP64 ? c->Dd.ipair : c->Df.ipair) != nullptr;
+  return pairs ? 0 : c->nc;
+}
+
 // Tiles of every phase for a tile size; heavier element tiles (hexes) are
 // queued before the interface tiles.
 int build_tiles(pdn_batch *b, int tile_items) {
@@ -434,7 +455,7 @@ int build_tiles(pdn_batch *b, int tile_items) {
   for (int p = 0; p < b->n; ++p) add(p, TK_CONTACT, b->plates[p]->ns);
   b->tile_off[1] = (int32_t)t.size();
   for (int p = 0; p < b->n; ++p) add(p, TK_HEX, b->plates[p]->nh);
-  for (int p = 0; p < b->n; ++p) add(p, TK_COH, b->plates[p]->nc);
+  for (int p = 0; p < b->n; ++p) add(p, TK_COH, coh_items(b, p));
   b->tile_off[2] = (int32_t)t.size();
   for (int p = 0; p < b->n; ++p) add(p, TK_GATHER, b->plates[p]->nn);
   b->tile_off[3] = (int32_t)t.size();
@@ -444,7 +465,7 @@ int build_tiles(pdn_batch *b, int tile_items) {
   for (int p = 0; p < b->n; ++p) {
     auto tiles = [&](int64_t n) { return (int)((n + tile_items - 1) / tile_items); };
     const pdn_ctx *c = b->plates[p];
-    nt[p] = make_int4(tiles(c->ns), tiles(c->nh) + tiles(c->nc), tiles(c->nn), 1);
+    nt[p] = make_int4(tiles(c->ns), tiles(c->nh) + tiles(coh_items(b, p)), tiles(c->nn), 1);
   }
   PB_CU(cudaMemcpy(b->d_ntiles, nt.data(), sizeof(int4) * b->n, cudaMemcpyHostToDevice), "upload tile counts");
   if (t.size() > b->tiles_cap) {
@@ -774,12 +795,6 @@ static int pdn_batch_init_body(pdn_batch **out, int32_t n_plates, const pdn_mesh
   for (int p = 0; p < n_plates; ++p) {
     int rc = pdn_init_mesh(&b->plates[p], &meshes[p], &mats[p], &o);
     if (rc) return fail_init(rc, "plate " + std::to_string(p) + ": " + pdn_last_error(nullptr));
-    // the batched kernel evaluates interface elements, so the plate keeps
-    // their thresholds in the element layout (no node pairs)
-    b->plates[p]->Df.ipair = nullptr;
-    b->plates[p]->Dd.ipair = nullptr;
-    b->plates[p]->Df.pair_layer = 0;
-    b->plates[p]->Dd.pair_layer = 0;
   }
   int rc = b->precision == PDN_FP64 ? upload_records<double>(b) : upload_records<float>(b);
   if (rc) return fail_init(rc, b->err);

@@ -156,9 +156,9 @@ def test_internal_force_equals_interface_elements(pkg, monkeypatch):
 
 
 def test_pairs_are_the_default_where_the_mesh_allows(pkg, monkeypatch):
-    """Node pairs on the benchmark plates (no column sweep unless asked for);
-    none without interfaces, with PDN_COH_PAIRS=0, or in a batch plate (the
-    batched kernel evaluates interface elements)."""
+    """Node pairs on the benchmark plates (no column sweep unless asked for)
+    and in the plates of a batch (the batched kernel's gather evaluates them
+    too); none without interfaces or with PDN_COH_PAIRS=0."""
     monkeypatch.delenv("PDN_SWEEP", raising=False)
     monkeypatch.delenv("PDN_COH_PAIRS", raising=False)
     w = pi.damage_fp32_plate()
@@ -173,7 +173,7 @@ def test_pairs_are_the_default_where_the_mesh_allows(pkg, monkeypatch):
     w = pi.damage_fp32_plate(nx=8, ny=12, plies=4, Lx=4.0, Ly=6.0, H=1.1)
     bt = pkg.pdn_batch_init([w.plate, w.plate], [w.material, w.material])
     for p in range(2):
-        assert pkg.pdn_get_info(pkg.pdn_batch_plate(bt, p))["coh_pairs"] == 0
+        assert pkg.pdn_get_info(pkg.pdn_batch_plate(bt, p))["coh_pairs"] == 2
     bt.close()
     monkeypatch.setenv("PDN_COH_PAIRS", "0")
     c = pkg.pdn_init_mesh(w.plate, w.material, precision=pkg.PDN_FP32_FORCE)
