@@ -20,6 +20,10 @@ __device__ __forceinline__ double xexp(double x) { return exp(x); }
 __device__ __forceinline__ float xcbrt(float x) { return cbrtf(x); }
 __device__ __forceinline__ double xcbrt(double x) { return cbrt(x); }
 __device__ __forceinline__ float xpow(float x, float y) { return powf(x, y); }
+// Correctly rounded reciprocals (the same value as 1 / x under IEEE
+// division, without the division's general path).
+__device__ __forceinline__ float xrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double xrcp(double x) { return __drcp_rn(x); }
 __device__ __forceinline__ double xpow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ bool xfinite(double x) { return isfinite(x); }
 __device__ __forceinline__ bool xfinite(float x) { return isfinite(x); }
@@ -280,9 +284,9 @@ __device__ __forceinline__ ElemLaw<T> elem_law(const Mat<T> &M, int64_t e) {
   L.XT = M.XT * f0;
   L.YT = M.YT * f1;
   L.SL = M.SL * f2;
-  L.iXT = T(1) / L.XT;
-  L.iYT = T(1) / L.YT;
-  const T iSL = T(1) / L.SL;
+  L.iXT = xrcp(L.XT);
+  L.iYT = xrcp(L.YT);
+  const T iSL = xrcp(L.SL);
   L.iSL2 = iSL * iSL;
   L.etaL = L.SL * M.etaLc;
   return L;

@@ -244,9 +244,9 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
     to_modes(ua, bm);
     const float J0 = 0.5f * ex, J1 = 0.5f * ey, J2 = 0.5f * ez;
     const float det = J0 * (J1 * J2);
-    jd[0] = 1.0f / J0;
-    jd[1] = 1.0f / J1;
-    jd[2] = 1.0f / J2;
+    jd[0] = xrcp(J0);
+    jd[1] = xrcp(J1);
+    jd[2] = xrcp(J2);
     wd[0] = det * jd[0];
     wd[1] = det * jd[1];
     wd[2] = det * jd[2];
@@ -265,12 +265,17 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
 #pragma unroll 1
   for (int p = 0; p < 4; ++p) {
     const int gx = pair_point(p, 0), gy = pair_point(p, 1);
-    // the pair's history, in flight while the strains are computed
+    // the pair's history, in flight while the strains are computed; an
+    // element with the initial history takes it without a load (a branch,
+    // uniform over the warp wherever its elements are all pristine)
     float2 h[7];
+    if (pristine_in) {
 #pragma unroll
-    for (int f = 0; f < 7; ++f)
-      h[f] = pristine_in ? p2(f < 4 ? 1.0f : 0.0f)
-                         : make_float2(hin[(int64_t)(f * 8 + gx) * nh], hin[(int64_t)(f * 8 + gy) * nh]);
+      for (int f = 0; f < 7; ++f) h[f] = p2(f < 4 ? 1.0f : 0.0f);
+    } else {
+#pragma unroll
+      for (int f = 0; f < 7; ++f) h[f] = make_float2(hin[(int64_t)(f * 8 + gx) * nh], hin[(int64_t)(f * 8 + gy) * nh]);
+    }
     const float et = (p & 1) ? gp : -gp, ze = (p & 2) ? gp : -gp;
     const float etze = et * ze;
     // H = du/dX: the xi column is the same in both lanes; the eta and zeta
@@ -375,9 +380,11 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
         hout[(int64_t)(f * 8 + gy) * nh] = h[f].y;
       }
     } else {
-      const bool changed = h[0].x > 1.0f || h[1].x > 1.0f || h[2].x > 1.0f || h[3].x > 1.0f || h[4].x != 0.0f ||
-                           h[5].x != 0.0f || h[6].x != 0.0f || h[0].y > 1.0f || h[1].y > 1.0f ||
-                           h[2].y > 1.0f || h[3].y > 1.0f || h[4].y != 0.0f || h[5].y != 0.0f || h[6].y != 0.0f;
+      // a pair that passed the elastic test kept the initial history
+      const bool changed = !elastic &&
+                           (h[0].x > 1.0f || h[1].x > 1.0f || h[2].x > 1.0f || h[3].x > 1.0f || h[4].x != 0.0f ||
+                            h[5].x != 0.0f || h[6].x != 0.0f || h[0].y > 1.0f || h[1].y > 1.0f ||
+                            h[2].y > 1.0f || h[3].y > 1.0f || h[4].y != 0.0f || h[5].y != 0.0f || h[6].y != 0.0f);
       if (changed && !dirty) {
         // first change in a pristine element: the points of the earlier
         // pairs keep the initial history, not yet in the output buffer
@@ -417,17 +424,39 @@ __device__ __forceinline__ void hex_box_pairs_core(const Dev<float> &D, const Ma
     // (xi-even modes) and difference (xi-odd modes)
     const float e0 = et * wd[0], z1 = ze * wd[1], e2 = et * wd[2], z0 = ze * wd[0], ez0 = etze * wd[0];
     const float g1 = gp * wd[1], g2 = gp * wd[2], gz1 = g1 * ze, ge2 = g2 * et;
-#pragma unroll
-    for (int I = 0; I < 3; ++I) {
-      const float s0 = P[0][I].x + P[0][I].y, s1 = P[1][I].x + P[1][I].y, s2s = P[2][I].x + P[2][I].y;
-      const float d1 = P[1][I].y - P[1][I].x, d2 = P[2][I].y - P[2][I].x;
-      C[1][I] += wd[0] * s0;
-      C[2][I] += wd[1] * s1;
-      C[3][I] += wd[2] * s2s;
-      C[4][I] += e0 * s0 + g1 * d1;
-      C[5][I] += z1 * s1 + e2 * s2s;
-      C[6][I] += z0 * s0 + g2 * d2;
-      C[7][I] += ez0 * s0 + gz1 * d1 + ge2 * d2;
+    // components 0 and 1 as a packed pair, component 2 alone
+    {
+      const float2 s0 = make_float2(P[0][0].x + P[0][0].y, P[0][1].x + P[0][1].y);
+      const float2 s1 = make_float2(P[1][0].x + P[1][0].y, P[1][1].x + P[1][1].y);
+      const float2 s2s = make_float2(P[2][0].x + P[2][0].y, P[2][1].x + P[2][1].y);
+      const float2 d1 = make_float2(P[1][0].y - P[1][0].x, P[1][1].y - P[1][1].x);
+      const float2 d2 = make_float2(P[2][0].y - P[2][0].x, P[2][1].y - P[2][1].x);
+      float2 c;
+      c = pfma(p2(wd[0]), s0, make_float2(C[1][0], C[1][1]));
+      C[1][0] = c.x, C[1][1] = c.y;
+      c = pfma(p2(wd[1]), s1, make_float2(C[2][0], C[2][1]));
+      C[2][0] = c.x, C[2][1] = c.y;
+      c = pfma(p2(wd[2]), s2s, make_float2(C[3][0], C[3][1]));
+      C[3][0] = c.x, C[3][1] = c.y;
+      c = padd(make_float2(C[4][0], C[4][1]), pfma(p2(g1), d1, pmul(p2(e0), s0)));
+      C[4][0] = c.x, C[4][1] = c.y;
+      c = padd(make_float2(C[5][0], C[5][1]), pfma(p2(e2), s2s, pmul(p2(z1), s1)));
+      C[5][0] = c.x, C[5][1] = c.y;
+      c = padd(make_float2(C[6][0], C[6][1]), pfma(p2(g2), d2, pmul(p2(z0), s0)));
+      C[6][0] = c.x, C[6][1] = c.y;
+      c = padd(make_float2(C[7][0], C[7][1]), pfma(p2(ge2), d2, pfma(p2(gz1), d1, pmul(p2(ez0), s0))));
+      C[7][0] = c.x, C[7][1] = c.y;
+    }
+    {
+      const float s0 = P[0][2].x + P[0][2].y, s1 = P[1][2].x + P[1][2].y, s2s = P[2][2].x + P[2][2].y;
+      const float d1 = P[1][2].y - P[1][2].x, d2 = P[2][2].y - P[2][2].x;
+      C[1][2] = fmaf(wd[0], s0, C[1][2]);
+      C[2][2] = fmaf(wd[1], s1, C[2][2]);
+      C[3][2] = fmaf(wd[2], s2s, C[3][2]);
+      C[4][2] = C[4][2] + fmaf(g1, d1, e0 * s0);
+      C[5][2] = C[5][2] + fmaf(e2, s2s, z1 * s1);
+      C[6][2] = C[6][2] + fmaf(g2, d2, z0 * s0);
+      C[7][2] = C[7][2] + fmaf(ge2, d2, fmaf(gz1, d1, ez0 * s0));
     }
   }
   if (D.pflag[0] != nullptr) D.pflag[hb ^ 1][e] = (pristine_in && !dirty) ? 1 : 0;
