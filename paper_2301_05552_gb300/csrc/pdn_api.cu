@@ -453,12 +453,51 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   if (ns > 0 && !mesh->surf) return bad("surf is NULL with n_surf > 0");
   if (mesh->n_plies < 1 || mesh->n_plies > kMaxPlies) return bad("n_plies must be in 1..64");
   if (opt->precision != PDN_FP64 && opt->precision != PDN_FP32_FORCE) return bad("unknown precision");
-  for (int64_t k = 0; k < nh * 8; ++k)
-    if (mesh->hex[k] < 0 || mesh->hex[k] >= nn) return bad("hex node id out of range");
-  for (int64_t k = 0; k < nc * 8; ++k)
-    if (mesh->coh[k] < 0 || mesh->coh[k] >= nn) return bad("interface node id out of range");
-  for (int64_t e = 0; e < nh; ++e)
-    if (mesh->ply_of_hex[e] < 0 || mesh->ply_of_hex[e] >= mesh->n_plies) return bad("ply id out of range");
+  // The loops over elements and nodes of the set-up run on the host's cores
+  // in contiguous chunks; every result is the same for any number of threads
+  // (per-thread partial results are combined in a fixed order).
+  const int n_threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
+  auto parallel_chunks = [&](int64_t n, auto &&body) {
+    const int nt = n < 4096 ? 1 : n_threads;
+    const int64_t chunk = (n + nt - 1) / nt;
+    if (nt == 1) {
+      body(int64_t(0), n, 0);
+      return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) {
+      const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
+      if (b >= e) continue;
+      // a chunk whose thread cannot be started runs here (no exception may
+      // leave the library)
+      try {
+        th.emplace_back([&, b, e, t]() { body(b, e, t); });
+      } catch (...) {
+        body(b, e, t);
+      }
+    }
+    for (auto &x : th) x.join();
+  };
+  // index of the first item in [0, n) for which fails(i) holds, or -1
+  auto first_failing = [&](int64_t n, auto &&fails) {
+    std::vector<int64_t> first(n_threads, -1);
+    parallel_chunks(n, [&](int64_t b, int64_t e, int t) {
+      for (int64_t i = b; i < e; ++i)
+        if (fails(i)) {
+          first[t] = i;
+          return;
+        }
+    });
+    for (int t = 0; t < n_threads; ++t)
+      if (first[t] >= 0) return first[t];
+    return int64_t(-1);
+  };
+  if (first_failing(nh * 8, [&](int64_t k) { return mesh->hex[k] < 0 || mesh->hex[k] >= nn; }) >= 0)
+    return bad("hex node id out of range");
+  if (first_failing(nc * 8, [&](int64_t k) { return mesh->coh[k] < 0 || mesh->coh[k] >= nn; }) >= 0)
+    return bad("interface node id out of range");
+  if (first_failing(nh, [&](int64_t e) { return mesh->ply_of_hex[e] < 0 || mesh->ply_of_hex[e] >= mesh->n_plies; }) >= 0)
+    return bad("ply id out of range");
   std::vector<int32_t> surf_of(nn, -1);
   for (int64_t s = 0; s < ns; ++s) {
     const int32_t j = mesh->surf[s];
@@ -470,11 +509,13 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   int32_t surf_base = ns > 0 ? mesh->surf[0] : -1;
   for (int64_t s = 1; s < ns && surf_base >= 0; ++s)
     if (mesh->surf[s] != mesh->surf[0] + s) surf_base = -1;
-  for (int64_t c = 0; c < nc; ++c)
-    for (int a = 0; a < 4; ++a)
-      for (int i = 0; i < 3; ++i)
-        if (mesh->X[i * nn + mesh->coh[c * 8 + a]] != mesh->X[i * nn + mesh->coh[c * 8 + a + 4]])
-          return bad("interface element faces must coincide in the reference configuration (zero thickness)");
+  if (first_failing(nc, [&](int64_t c) {
+        for (int a = 0; a < 4; ++a)
+          for (int i = 0; i < 3; ++i)
+            if (mesh->X[i * nn + mesh->coh[c * 8 + a]] != mesh->X[i * nn + mesh->coh[c * 8 + a + 4]]) return true;
+        return false;
+      }) >= 0)
+    return bad("interface element faces must coincide in the reference configuration (zero thickness)");
   if (mesh->fixed)
     for (int64_t j = 0; j < nn; ++j)
       if (mesh->fixed[j] > 7) return bad("fixed entries must be constraint bits 0..7");
@@ -506,30 +547,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // element's nodal mass contributions (summed over its Gauss points) go to
   // its own slots, and the nodes sum them afterwards in element order, so the
   // result does not depend on the number of threads.
-  const int n_threads = std::max(1, std::min(16, (int)std::thread::hardware_concurrency()));
-  auto parallel_chunks = [&](int64_t n, auto &&body) {
-    const int nt = n < 4096 ? 1 : n_threads;
-    const int64_t chunk = (n + nt - 1) / nt;
-    if (nt == 1) {
-      body(int64_t(0), n, 0);
-      return;
-    }
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) {
-      const int64_t b = t * chunk, e = std::min<int64_t>(n, b + chunk);
-      if (b >= e) continue;
-      // a chunk whose thread cannot be started runs here (no exception may
-      // leave the library)
-      try {
-        th.emplace_back([&, b, e, t]() { body(b, e, t); });
-      } catch (...) {
-        body(b, e, t);
-      }
-    }
-    for (auto &x : th) x.join();
-  };
   std::vector<double> mass(nn, 0.0);
   std::vector<double> vol(nh);
+  std::vector<double> cm;  // [nh][8] each element's nodal mass contributions
   double cmax = 0.0;
   {
     Mat<double> tmp{};
@@ -542,7 +562,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   double dtb = INFINITY;
   const double sqrho = std::sqrt(m.rho / cmax);
   {
-    std::vector<double> cm((size_t)nh * 8);
+    cm.resize((size_t)nh * 8);
     std::vector<double> dtb_t(n_threads, INFINITY);
     std::vector<int64_t> bad_t(n_threads, -1);
     parallel_chunks(nh, [&](int64_t b, int64_t e1, int t) {
@@ -569,8 +589,6 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       if (bad_t[t] >= 0)
         return die(PDN_E_ARG, "hex with non-positive Jacobian (element " + std::to_string(bad_t[t]) + ")");
     for (int t = 0; t < n_threads; ++t) dtb = std::min(dtb, dtb_t[t]);
-    for (int64_t e = 0; e < nh; ++e)
-      for (int a = 0; a < 8; ++a) mass[mesh->hex[e * 8 + a]] += cm[e * 8 + a];
   }
   // Axis-aligned boxes whose corner coordinates coincide exactly in pairs in
   // the element precision: then the higher trilinear modes of X vanish
@@ -587,8 +605,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
              P(0, 2) == P(1, 2) && P(0, 2) == P(2, 2) && P(0, 2) == P(3, 2) && P(4, 2) == P(5, 2) &&
              P(4, 2) == P(6, 2) && P(4, 2) == P(7, 2);
     };
-    for (int64_t e = 0; e < nh && all_boxes; ++e)
-      all_boxes = opt->precision == PDN_FP64 ? is_box(e, double{}) : is_box(e, float{});
+    all_boxes = first_failing(nh, [&](int64_t e) {
+                  return !(opt->precision == PDN_FP64 ? is_box(e, double{}) : is_box(e, float{}));
+                }) < 0;
   }
   bool all_flat_coh = true;
   {
@@ -600,21 +619,42 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
              P(0, 2) == P(1, 2) && P(0, 2) == P(2, 2) && P(0, 2) == P(3, 2) && P(1, 0) > P(0, 0) &&
              P(3, 1) > P(0, 1);
     };
-    for (int64_t c = 0; c < nc && all_flat_coh; ++c)
-      all_flat_coh = opt->precision == PDN_FP64 ? is_flat(c, double{}) : is_flat(c, float{});
+    all_flat_coh = first_failing(nc, [&](int64_t c) {
+                     return !(opt->precision == PDN_FP64 ? is_flat(c, double{}) : is_flat(c, float{}));
+                   }) < 0;
   }
-  // node -> element-force slot CSR (hexes ascending, then interfaces ascending)
-  std::vector<int32_t> row(nn + 1, 0), col((size_t)(nh + nc) * 8);
-  for (int64_t k = 0; k < nh * 8; ++k) row[mesh->hex[k] + 1]++;
-  for (int64_t k = 0; k < nc * 8; ++k) row[mesh->coh[k] + 1]++;
+  // node -> element-force slot CSR (hexes ascending, then interfaces
+  // ascending).  Slot k of the entry list is 8 e + a for hexes and
+  // 8 (n_hex + c) + a for interfaces, so each row is its slots in ascending
+  // order: counted and filled at atomic cursors from the threads' chunks,
+  // then every row sorted, which makes it independent of their interleaving.
+  const int64_t n_ent = (nh + nc) * 8;
+  std::vector<int32_t> row(nn + 1, 0), col((size_t)n_ent);
+  auto node_of = [&](int64_t k) { return k < nh * 8 ? mesh->hex[k] : mesh->coh[k - nh * 8]; };
+  parallel_chunks(n_ent, [&](int64_t b, int64_t e, int) {
+    for (int64_t k = b; k < e; ++k) __atomic_fetch_add(&row[node_of(k) + 1], 1, __ATOMIC_RELAXED);
+  });
   for (int64_t j = 0; j < nn; ++j) row[j + 1] += row[j];
   {
     std::vector<int32_t> fill(row.begin(), row.end() - 1);
-    for (int64_t e = 0; e < nh; ++e)
-      for (int a = 0; a < 8; ++a) col[fill[mesh->hex[e * 8 + a]]++] = (int32_t)(e * 8 + a);
-    for (int64_t c = 0; c < nc; ++c)
-      for (int a = 0; a < 8; ++a) col[fill[mesh->coh[c * 8 + a]]++] = (int32_t)((nh + c) * 8 + a);
+    parallel_chunks(n_ent, [&](int64_t b, int64_t e, int) {
+      for (int64_t k = b; k < e; ++k) col[__atomic_fetch_add(&fill[node_of(k)], 1, __ATOMIC_RELAXED)] = (int32_t)k;
+    });
   }
+  parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+    for (int64_t j = b; j < e; ++j) std::sort(col.begin() + row[j], col.begin() + row[j + 1]);
+  });
+  // lumped mass: each node sums its hexes' contributions in element order
+  // (its CSR row), the same sum for any number of threads
+  parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+    for (int64_t j = b; j < e; ++j) {
+      double mj = 0.0;
+      for (int32_t r = row[j]; r < row[j + 1]; ++r)
+        if (col[r] < nh * 8) mj += cm[col[r]];
+      mass[j] = mj;
+    }
+  });
+  std::vector<double>().swap(cm);
   // Slots of the element forces.  When no node has more than eight
   // incident elements (every structured laminate: 8 hexes inside a layer,
   // 4 hexes and 4 interfaces on an interface layer), node j owns slots
@@ -622,21 +662,23 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // reads a node's slots in the same load round as its state, without the
   // CSR row first, and sums them in the same order.  Otherwise the slots are
   // the CSR positions.
-  int32_t maxdeg = 0;
-  for (int64_t j = 0; j < nn; ++j) maxdeg = std::max(maxdeg, row[j + 1] - row[j]);
-  const bool ell = maxdeg <= 8 && 8 * nn <= INT32_MAX;
+  const bool ell = first_failing(nn, [&](int64_t j) { return row[j + 1] - row[j] > 8; }) < 0 && 8 * nn <= INT32_MAX;
   const int64_t n_slots = ell ? 8 * nn : 8 * (nh + nc);
   std::vector<int32_t> pos(col.size());
-  for (int64_t j = 0; j < nn; ++j)
-    for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = ell ? (int32_t)(8 * j + (r - row[j])) : r;
+  parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+    for (int64_t j = b; j < e; ++j)
+      for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = ell ? (int32_t)(8 * j + (r - row[j])) : r;
+  });
   std::vector<uint32_t> rank(ell ? nh + nc : 0);
   if (ell) {
-    for (int64_t e = 0; e < nh + nc; ++e) {
-      const int32_t *cn = e < nh ? mesh->hex + e * 8 : mesh->coh + (e - nh) * 8;
-      uint32_t w = 0;
-      for (int a = 0; a < 8; ++a) w |= (uint32_t)(pos[e * 8 + a] - 8 * cn[a]) << (3 * a);
-      rank[e] = w;
-    }
+    parallel_chunks(nh + nc, [&](int64_t b, int64_t e1, int) {
+      for (int64_t e = b; e < e1; ++e) {
+        const int32_t *cn = e < nh ? mesh->hex + e * 8 : mesh->coh + (e - nh) * 8;
+        uint32_t w = 0;
+        for (int a = 0; a < 8; ++a) w |= (uint32_t)(pos[e * 8 + a] - 8 * cn[a]) << (3 * a);
+        rank[e] = w;
+      }
+    });
   }
   // column sweep (FP32 box hexes, flat interfaces, eight slots per node),
   // planned only on request (PDN_SWEEP=1, read here): it measured slower
@@ -678,48 +720,73 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       ipair.assign(nn, int2{-1, 0});
       iw.assign(sizeof(T) * 4 * nn, 0);
       T *wn = reinterpret_cast<T *>(iw.data());
-      bool first = true;
-      T w0 = T(0);
-      for (int64_t j = 0; j < nn; ++j) {
-        int nhx = 0, kc = 0, top = 0;
-        int32_t partner = -1;
-        for (int32_t r = row[j]; r < row[j + 1]; ++r) {
-          const int32_t slot = col[r];
-          if (slot < nh * 8) {
-            if (kc) return false;  // hexes first (CSR order)
-            ++nhx;
-            continue;
+      // per thread: the first weight it met, whether all its weights equal
+      // it, whether all its nodes qualify
+      std::vector<T> w_first(n_threads, T(0));
+      std::vector<char> has_w(n_threads, 0), same_w(n_threads, 1), ok_t(n_threads, 1);
+      parallel_chunks(nn, [&](int64_t b, int64_t e, int t) {
+        for (int64_t j = b; j < e; ++j) {
+          int nhx = 0, kc = 0, top = 0;
+          int32_t partner = -1;
+          for (int32_t r = row[j]; r < row[j + 1]; ++r) {
+            const int32_t slot = col[r];
+            if (slot < nh * 8) {
+              if (kc) {  // hexes first (CSR order)
+                ok_t[t] = 0;
+                return;
+              }
+              ++nhx;
+              continue;
+            }
+            const int64_t c = slot / 8 - nh;
+            const int a = slot % 8;
+            const int32_t *q = mesh->coh + c * 8;
+            const int32_t pj = q[a ^ 4];
+            const int tp = a >= 4 ? 1 : 0;
+            if (kc == 0) {
+              partner = pj;
+              top = tp;
+            } else if (pj != partner || tp != top || kc == 4) {
+              ok_t[t] = 0;
+              return;
+            }
+            const T x0 = (T)mesh->X[q[0]], x2 = (T)mesh->X[q[2]];
+            const T y0 = (T)mesh->X[nn + q[0]], y2 = (T)mesh->X[nn + q[2]];
+            const T w = T(0.25) * (x2 - x0) * (y2 - y0);
+            wn[4 * j + kc] = w;
+            if (!has_w[t]) {
+              w_first[t] = w;
+              has_w[t] = 1;
+            } else if (w != w_first[t]) {
+              same_w[t] = 0;
+            }
+            ++kc;
           }
-          const int64_t c = slot / 8 - nh;
-          const int a = slot % 8;
-          const int32_t *q = mesh->coh + c * 8;
-          const int32_t pj = q[a ^ 4];
-          const int tp = a >= 4 ? 1 : 0;
-          if (kc == 0) {
-            partner = pj;
-            top = tp;
-          } else if (pj != partner || tp != top || kc == 4) {
-            return false;
+          if (nhx > 8 || partner == (int32_t)j) {
+            ok_t[t] = 0;
+            return;
           }
-          const T x0 = (T)mesh->X[q[0]], x2 = (T)mesh->X[q[2]];
-          const T y0 = (T)mesh->X[nn + q[0]], y2 = (T)mesh->X[nn + q[2]];
-          const T w = T(0.25) * (x2 - x0) * (y2 - y0);
-          wn[4 * j + kc] = w;
-          if (first) {
-            w0 = w;
-            first = false;
-          } else if (w != w0) {
-            pairs_uniform = false;
-          }
-          ++kc;
+          ipair[j] = int2{partner, kc | (top << 3) | (nhx << 4)};
         }
-        if (nhx > 8 || partner == (int32_t)j) return false;
-        ipair[j] = int2{partner, kc | (top << 3) | (nhx << 4)};
+      });
+      T w0 = T(0);
+      bool first = true;
+      for (int t = 0; t < n_threads; ++t) {
+        if (!ok_t[t]) return false;
+        if (!has_w[t]) continue;
+        if (!same_w[t]) pairs_uniform = false;
+        if (first) {
+          w0 = w_first[t];
+          first = false;
+        } else if (w_first[t] != w0) {
+          pairs_uniform = false;
+        }
       }
-      for (int64_t j = 0; j < nn; ++j) {
-        const int32_t pj = ipair[j].x;
-        if (pj >= 0 && (ipair[pj].x != (int32_t)j || ((ipair[pj].y ^ ipair[j].y) & 8) == 0)) return false;
-      }
+      if (first_failing(nn, [&](int64_t j) {
+            const int32_t pj = ipair[j].x;
+            return pj >= 0 && (ipair[pj].x != (int32_t)j || ((ipair[pj].y ^ ipair[j].y) & 8) == 0);
+          }) >= 0)
+        return false;
       coh_w = (double)w0;
       return true;
     };
@@ -733,18 +800,20 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       for (int64_t j = 0; j < nn && L == 0; ++j)
         if (ipair[j].x >= 0) L = std::llabs((int64_t)ipair[j].x - j);
       bool ok = L > 0 && nn % L == 0 && nn / L <= kMaxPairLayers;
-      for (int64_t l = 0; ok && l < nn / L; ++l) {
-        const int64_t j0 = l * L;
-        const int kind = ipair[j0].x < 0 ? 0 : (((ipair[j0].y >> 3) & 1) ? 2 : 1);
-        for (int64_t j = j0; ok && j < j0 + L; ++j) {
-          const int2 ip = ipair[j];
-          if (kind == 0)
-            ok = ip.x < 0;
-          else
-            ok = ip.x == (kind == 1 ? j + L : j - L) && ((ip.y >> 3) & 1) == (kind == 2 ? 1 : 0) &&
-                 ((ip.y >> 4) & 15) <= 4;
+      if (ok) {
+        // each node against its layer's kind (that of the layer's first node)
+        auto kind_of = [&](int64_t j) { return ipair[j].x < 0 ? 0 : (((ipair[j].y >> 3) & 1) ? 2 : 1); };
+        ok = first_failing(nn, [&](int64_t j) {
+               const int kind = kind_of((j / L) * L);
+               const int2 ip = ipair[j];
+               if (kind == 0) return ip.x >= 0;
+               return !(ip.x == (kind == 1 ? j + L : j - L) && ((ip.y >> 3) & 1) == (kind == 2 ? 1 : 0) &&
+                        ((ip.y >> 4) & 15) <= 4);
+             }) < 0;
+        for (int64_t l = 0; ok && l < nn / L; ++l) {
+          const int kind = kind_of(l * L);
+          if (kind) pair_mask[kind - 1][l >> 6] |= uint64_t(1) << (l & 63);
         }
-        if (ok && kind) pair_mask[kind - 1][l >> 6] |= uint64_t(1) << (l & 63);
       }
       if (ok) pair_layer = (int32_t)L;
     }
@@ -800,8 +869,10 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   const double safety = opt->dt_safety > 0 ? opt->dt_safety : 0.5;
   ctx->dt = opt->dt > 0 ? opt->dt : safety * std::min(dtb, dtc);
   if (!(ctx->dt > 0) || !std::isfinite(ctx->dt)) return die(PDN_E_UNSTABLE, "no finite stable time step");
-  for (int64_t j = 0; j < nn; ++j)
-    if (!(mass[j] > 0)) return die(PDN_E_ARG, "node " + std::to_string(j) + " has no mass (not in any hex)");
+  {
+    const int64_t j = first_failing(nn, [&](int64_t k) { return !(mass[k] > 0); });
+    if (j >= 0) return die(PDN_E_ARG, "node " + std::to_string(j) + " has no mass (not in any hex)");
+  }
 
   // --- device arena ---------------------------------------------------------
   const bool fp64 = ctx->precision == PDN_FP64;
@@ -908,16 +979,19 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
 
   // host-side staging of the uploads
   std::vector<uint8_t> nflag(nn, 0);
-  for (int64_t j = 0; j < nn; ++j) {
-    nflag[j] = mesh->fixed ? mesh->fixed[j] : 0;
-    if (surf_of[j] >= 0) nflag[j] |= 8;
-    if (pairs_on && ipair[j].x >= 0) nflag[j] |= (uint8_t)((ipair[j].y & 7) << kFlagPairShift);
-  }
+  parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+    for (int64_t j = b; j < e; ++j) {
+      nflag[j] = mesh->fixed ? mesh->fixed[j] : 0;
+      if (surf_of[j] >= 0) nflag[j] |= 8;
+      if (pairs_on && ipair[j].x >= 0) nflag[j] |= (uint8_t)((ipair[j].y & 7) << kFlagPairShift);
+    }
+  });
   std::vector<double> Xs(3 * std::max<int64_t>(ns, 1), 0.0);
   for (int64_t s = 0; s < ns; ++s)
     for (int i = 0; i < 3; ++i) Xs[i * ns + s] = mesh->X[i * nn + mesh->surf[s]];
   std::vector<char> X4(ts * 4 * nn), imass(ts * nn);
-  for (int64_t j = 0; j < nn; ++j) {
+  parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+  for (int64_t j = b; j < e; ++j) {
     if (fp64) {
       double *q = reinterpret_cast<double *>(X4.data()) + 4 * j;
       q[0] = mesh->X[j];
@@ -934,6 +1008,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       reinterpret_cast<float *>(imass.data())[j] = (float)(1.0 / mass[j]);
     }
   }
+  });
   auto up = [&](void *dst, const void *src, size_t bytes) {
     return bytes ? cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
   };
