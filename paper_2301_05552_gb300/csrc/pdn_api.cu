@@ -254,18 +254,40 @@ int fill_mat(Mat<T> &M, const pdn_material &m, const double *ply_angle, int n_pl
 }
 
 // Hex8 geometry on the host (set-up only): det J and N_a at the 2x2x2 points.
+// Shape functions and their natural derivatives at the 2x2x2 Gauss points,
+// the same for every element: evaluated once.
+struct HexGaussTables {
+  double N[8][8];      // [point][node]
+  double dN[8][8][3];  // [point][node][xi, eta, zeta]
+};
+const HexGaussTables &hex_gauss_tables() {
+  static const HexGaussTables T = [] {
+    static const int S[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+    HexGaussTables t{};
+    const double gp = 1.0 / std::sqrt(3.0);
+    for (int g = 0; g < 8; ++g) {
+      const double xi = S[g][0] * gp, et = S[g][1] * gp, ze = S[g][2] * gp;
+      for (int a = 0; a < 8; ++a) {
+        const double sx = S[a][0], sy = S[a][1], sz = S[a][2];
+        t.dN[g][a][0] = 0.125 * sx * (1 + et * sy) * (1 + ze * sz);
+        t.dN[g][a][1] = 0.125 * sy * (1 + xi * sx) * (1 + ze * sz);
+        t.dN[g][a][2] = 0.125 * sz * (1 + xi * sx) * (1 + et * sy);
+        t.N[g][a] = 0.125 * (1 + xi * sx) * (1 + et * sy) * (1 + ze * sz);
+      }
+    }
+    return t;
+  }();
+  return T;
+}
+
 void hex_gauss(const double X[8][3], double detJ[8], double N[8][8]) {
-  static const int S[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
-                              {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
-  const double gp = 1.0 / std::sqrt(3.0);
+  const HexGaussTables &T = hex_gauss_tables();
   for (int g = 0; g < 8; ++g) {
-    const double xi = S[g][0] * gp, et = S[g][1] * gp, ze = S[g][2] * gp;
     double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     for (int a = 0; a < 8; ++a) {
-      const double sx = S[a][0], sy = S[a][1], sz = S[a][2];
-      const double dN[3] = {0.125 * sx * (1 + et * sy) * (1 + ze * sz), 0.125 * sy * (1 + xi * sx) * (1 + ze * sz),
-                            0.125 * sz * (1 + xi * sx) * (1 + et * sy)};
-      N[g][a] = 0.125 * (1 + xi * sx) * (1 + et * sy) * (1 + ze * sz);
+      const double *dN = T.dN[g][a];
+      N[g][a] = T.N[g][a];
       for (int i = 0; i < 3; ++i)
         for (int k = 0; k < 3; ++k) J[i][k] += X[a][i] * dN[k];
     }
