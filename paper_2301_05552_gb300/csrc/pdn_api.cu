@@ -17,6 +17,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "pdn.h"
@@ -429,6 +430,28 @@ static int get_history_t(pdn_ctx *ctx, const Dev<T> &D, T *hist, T *rD) {
   return PDN_OK;
 }
 
+// A vector element type's allocator that leaves new elements uninitialised:
+// the set-up's large arrays are written in full by the threads' chunks, so
+// a serial zero fill (and its first-touch page faults on one core) is saved.
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  using std::allocator<T>::allocator;
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  template <typename U>
+  void construct(U *p) noexcept {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U *p, A &&...a) {
+    ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using RawVec = std::vector<T, NoInitAlloc<T>>;
+
 }  // namespace
 
 extern "C" {
@@ -569,9 +592,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // element's nodal mass contributions (summed over its Gauss points) go to
   // its own slots, and the nodes sum them afterwards in element order, so the
   // result does not depend on the number of threads.
-  std::vector<double> mass(nn, 0.0);
-  std::vector<double> vol(nh);
-  std::vector<double> cm;  // [nh][8] each element's nodal mass contributions
+  RawVec<double> mass(nn);  // every entry written by the per-node sums below
+  RawVec<double> vol(nh);
+  RawVec<double> cm;  // [nh][8] each element's nodal mass contributions
   double cmax = 0.0;
   {
     Mat<double> tmp{};
@@ -651,7 +674,8 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // order: counted and filled at atomic cursors from the threads' chunks,
   // then every row sorted, which makes it independent of their interleaving.
   const int64_t n_ent = (nh + nc) * 8;
-  std::vector<int32_t> row(nn + 1, 0), col((size_t)n_ent);
+  std::vector<int32_t> row(nn + 1, 0);
+  RawVec<int32_t> col((size_t)n_ent);
   auto node_of = [&](int64_t k) { return k < nh * 8 ? mesh->hex[k] : mesh->coh[k - nh * 8]; };
   parallel_chunks(n_ent, [&](int64_t b, int64_t e, int) {
     for (int64_t k = b; k < e; ++k) __atomic_fetch_add(&row[node_of(k) + 1], 1, __ATOMIC_RELAXED);
@@ -676,7 +700,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
       mass[j] = mj;
     }
   });
-  std::vector<double>().swap(cm);
+  RawVec<double>().swap(cm);
   // Slots of the element forces.  When no node has more than eight
   // incident elements (every structured laminate: 8 hexes inside a layer,
   // 4 hexes and 4 interfaces on an interface layer), node j owns slots
@@ -686,7 +710,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   // the CSR positions.
   const bool ell = first_failing(nn, [&](int64_t j) { return row[j + 1] - row[j] > 8; }) < 0 && 8 * nn <= INT32_MAX;
   const int64_t n_slots = ell ? 8 * nn : 8 * (nh + nc);
-  std::vector<int32_t> pos(col.size());
+  RawVec<int32_t> pos(col.size());
   parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
     for (int64_t j = b; j < e; ++j)
       for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = ell ? (int32_t)(8 * j + (r - row[j])) : r;
@@ -1000,7 +1024,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   if (ce != cudaSuccess) return die(PDN_E_CUDA, std::string("pinned allocation: ") + cudaGetErrorString(ce));
 
   // host-side staging of the uploads
-  std::vector<uint8_t> nflag(nn, 0);
+  RawVec<uint8_t> nflag(nn);
   parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
     for (int64_t j = b; j < e; ++j) {
       nflag[j] = mesh->fixed ? mesh->fixed[j] : 0;
@@ -1011,7 +1035,7 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   std::vector<double> Xs(3 * std::max<int64_t>(ns, 1), 0.0);
   for (int64_t s = 0; s < ns; ++s)
     for (int i = 0; i < 3; ++i) Xs[i * ns + s] = mesh->X[i * nn + mesh->surf[s]];
-  std::vector<char> X4(ts * 4 * nn), imass(ts * nn);
+  RawVec<char> X4(ts * 4 * nn), imass(ts * nn);
   parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
   for (int64_t j = b; j < e; ++j) {
     if (fp64) {
