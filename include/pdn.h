@@ -192,7 +192,10 @@ typedef struct {
                               the partner from the node id, 1 otherwise (a partner table).
                               0: interface elements (k_coh).  The environment
                               variable PDN_COH_PAIRS=0, read by pdn_init_mesh, keeps the
-                              interface elements */
+                              interface elements.  With 2, a node of an interface layer
+                              owns 4 element-force slots instead of 8 (its interface
+                              elements write none), unless PDN_SLOTS_COMPACT=0 is set at
+                              pdn_init_mesh */
   int32_t reserved;
   double tune_ms[12];      /* mean time of an internal-force pass with each variant when
                               tuned (0 if not): entries 0..3 the hex variants with separate

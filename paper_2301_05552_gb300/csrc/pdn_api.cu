@@ -755,6 +755,8 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
   bool pairs_on = false, pairs_uniform = true;
   int32_t pair_layer = 0;
   uint64_t pair_mask[2][2] = {{0, 0}, {0, 0}};
+  bool slot_compact = false;
+  int32_t layer_off[kMaxPairLayers] = {};  // compact slots: first slot of layer l minus l L width(l)
   std::vector<int2> ipair;
   std::vector<char> iw;  // [nn] 4 weights of the element precision
   double coh_w = 0.0;
@@ -862,6 +864,41 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
         }
       }
       if (ok) pair_layer = (int32_t)L;
+    }
+    // compact force slots (4 per interface-layer node): every hex's lower
+    // face in one node layer and its upper face in one; PDN_SLOTS_COMPACT=0,
+    // read here, keeps 8 slots per node
+    if (pair_layer > 0) {
+      const char *cv = std::getenv("PDN_SLOTS_COMPACT");
+      const bool want = !(cv && cv[0] == '0' && cv[1] == '\0');
+      const int64_t L = pair_layer;
+      auto faces_in_layers = [&](int64_t e) {
+        const int32_t *q = mesh->hex + e * 8;
+        return q[0] / L == q[1] / L && q[0] / L == q[2] / L && q[0] / L == q[3] / L && q[4] / L == q[5] / L &&
+               q[4] / L == q[6] / L && q[4] / L == q[7] / L;
+      };
+      // (node ids below 2^24, exact in FP32, for the device's layer lookup)
+      slot_compact = want && nn <= (int64_t(1) << 24) &&
+                     first_failing(nh, [&](int64_t e) { return !faces_in_layers(e); }) < 0;
+      if (slot_compact) {
+        // slot positions of the generic element path in the compact layout
+        const uint64_t m0 = pair_mask[0][0] | pair_mask[1][0], m1 = pair_mask[0][1] | pair_mask[1][1];
+        auto base_of = [&](int64_t j) {
+          const int64_t lay = j / L;
+          const int below = lay < 64 ? __builtin_popcountll(m0 & ((1ull << lay) - 1ull))
+                                     : __builtin_popcountll(m0) + __builtin_popcountll(m1 & ((1ull << (lay - 64)) - 1ull));
+          const bool pair = (((lay < 64 ? m0 : m1) >> (lay & 63)) & 1) != 0;
+          return L * (8 * lay - 4 * (int64_t)below) + (j - lay * L) * (pair ? 4 : 8);
+        };
+        parallel_chunks(nn, [&](int64_t b, int64_t e, int) {
+          for (int64_t j = b; j < e; ++j)
+            for (int32_t r = row[j]; r < row[j + 1]; ++r) pos[col[r]] = (int32_t)(base_of(j) + (r - row[j]));
+        });
+        for (int64_t l = 0; l < nn / L; ++l) {
+          const bool pair = (((l < 64 ? m0 : m1) >> (l & 63)) & 1) != 0;
+          layer_off[l] = (int32_t)(base_of(l * L) - l * L * (pair ? 4 : 8));
+        }
+      }
     }
     if (!pairs_on) {
       std::vector<int2>().swap(ipair);
@@ -1170,6 +1207,9 @@ static int pdn_init_mesh_body(pdn_ctx **out, const pdn_mesh_desc *mesh, const pd
     D.coh_w = (T)coh_w;
     for (int b = 0; b < 2; ++b) D.rDn[b] = pairs_on ? reinterpret_cast<T *>(P.rDn[b]) : nullptr;
     D.pair_layer = pair_layer;
+    D.slot_compact = slot_compact ? 1 : 0;
+    D.pair_inv_L = pair_layer > 0 ? 1.0f / (float)pair_layer : 0.0f;
+    for (int l = 0; l < kMaxPairLayers; ++l) D.layer_off[l] = layer_off[l];
     for (int k = 0; k < 2; ++k)
       for (int w = 0; w < 2; ++w) D.pair_mask[k][w] = pair_mask[k][w];
     D.nrm = d_nrm;

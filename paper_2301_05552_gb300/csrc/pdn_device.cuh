@@ -211,6 +211,28 @@ __device__ __forceinline__ void repeat_mark_nodes(uint8_t *mark, const int nd[8]
 }
 
 // ---------------------------------------------------------------------------
+// Compact force slots (Dev::slot_compact): the node layer of node j, whether
+// layer lay is an interface layer, and the first slot of node j in layer
+// lay.
+template <typename T>
+__device__ __forceinline__ uint32_t node_layer(const Dev<T> &D, int64_t j) {
+  const uint32_t L = (uint32_t)D.pair_layer, jj = (uint32_t)j;
+  uint32_t lay = (uint32_t)((float)jj * D.pair_inv_L);
+  if (lay * L > jj) --lay;
+  else if ((lay + 1) * L <= jj) ++lay;
+  return lay;
+}
+template <typename T>
+__device__ __forceinline__ bool layer_is_pair(const Dev<T> &D, uint32_t lay) {
+  const uint64_t m = lay < 64 ? (D.pair_mask[0][0] | D.pair_mask[1][0]) : (D.pair_mask[0][1] | D.pair_mask[1][1]);
+  return ((m >> (lay & 63)) & 1) != 0;
+}
+template <typename T>
+__device__ __forceinline__ int64_t compact_slot_base(const Dev<T> &D, uint32_t lay, int64_t j) {
+  return j * (layer_is_pair(D, lay) ? 4 : 8) + D.layer_off[lay];
+}
+
+// ---------------------------------------------------------------------------
 // Slots of an element's eight nodal forces.  With eight slots per node
 // (D.rank set) slot = 8 node + rank, the node ids re-read from the
 // connectivity (still in L1 from the element's start) and the ranks packed
@@ -222,8 +244,19 @@ __device__ __forceinline__ void element_slots(const Dev<T> &D, const int32_t *co
     const int4 c0 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e);
     const int4 c1 = __ldg(reinterpret_cast<const int4 *>(conn) + 2 * e + 1);
     const int nd[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    if (D.slot_compact) {
+      // a hex's lower face lies in one node layer, its upper face in one
+      // (checked by the host before it turns compact slots on)
+      const uint32_t lb = node_layer(D, nd[0]), lt = node_layer(D, nd[4]);
+      const int wb = layer_is_pair(D, lb) ? 4 : 8, wt = layer_is_pair(D, lt) ? 4 : 8;
+      const int ob = D.layer_off[lb], ot = D.layer_off[lt];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) ps[a] = 8 * nd[a] + (int)((rk >> (3 * a)) & 7u);
+      for (int a = 0; a < 8; ++a)
+        ps[a] = nd[a] * (a < 4 ? wb : wt) + (a < 4 ? ob : ot) + (int)((rk >> (3 * a)) & 7u);
+    } else {
+#pragma unroll
+      for (int a = 0; a < 8; ++a) ps[a] = 8 * nd[a] + (int)((rk >> (3 * a)) & 7u);
+    }
   } else {
     const int4 p0 = __ldg(pos2), p1 = __ldg(pos2 + 1);
     ps[0] = p0.x, ps[1] = p0.y, ps[2] = p0.z, ps[3] = p0.w;

@@ -134,6 +134,8 @@ struct Vec4T<double> {
   using type = double4_32a;  // 32-byte aligned: one 256-bit access per node
 };
 
+constexpr int kMaxPairLayers = 128;  // node layers a layered numbering may have
+
 // Pointers of a context's device state for the step kernels.
 template <typename T>
 struct Dev {
@@ -254,8 +256,18 @@ struct Dev {
   // interface elements.  0: partners from ipair (a second load round).
   int32_t pair_layer;
   uint64_t pair_mask[2][2];
+  // compact force slots of a layered numbering with node pairs: a node of an
+  // interface layer owns 4 slots (it has at most four hexes and its
+  // interface elements write none), any other node 8; layer l starts at slot
+  // L (8 l - 4 (interface layers below l)).  0: 8 slots per node
+  int32_t slot_compact;
+  // with compact slots: the first slot of node j of layer l is
+  // j * width(l) + layer_off[l] (width 4 on interface layers, 8 else), and
+  // l = j / pair_layer, found as the rounded product with pair_inv_L
+  // corrected by one either way
+  float pair_inv_L;
+  int32_t layer_off[kMaxPairLayers];
 };
-constexpr int kMaxPairLayers = 128;
 constexpr int kFlagPairShift = 4;  // node flag bits 4-6: incident interface elements
 
 // Launchers (pdn_kernels.cu).

@@ -1486,7 +1486,7 @@ __device__ __forceinline__ void gather_pair_layered_item(const Dev<T> &D, const 
   node_state_load(D, j, mode, q);
   const uint8_t fl = D.nflag[j];
   const int64_t pj = upper ? j - (int64_t)L : j + (int64_t)L;
-  const V4 *fs = D.fe + 8 * j;
+  const V4 *fs = D.fe + (D.slot_compact ? compact_slot_base(D, lay, j) : 8 * j);
   V4 f[8];
 #pragma unroll
   for (int k = 0; k < 4; ++k) f[k] = fs[k];
