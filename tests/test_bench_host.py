@@ -150,3 +150,12 @@ def test_bench_functions_use_only_defined_names():
                 if n.id not in local and n.id not in module and not hasattr(builtins, n.id):
                     missing.append(f"{fn.name}:{n.lineno}:{n.id}")
     assert not missing, missing
+
+
+def test_kernels_per_pass():
+    """Four kernels a pass with node pairs or the mixed element kernel,
+    five with a separate interface kernel, four without interfaces."""
+    assert bench.kernels_per_pass({"coh_pairs": 2, "hex_variant": 0}, 100) == 4
+    assert bench.kernels_per_pass({"coh_pairs": 0, "hex_variant": 0}, 100) == 5
+    assert bench.kernels_per_pass({"coh_pairs": 0, "hex_variant": 5}, 100) == 4
+    assert bench.kernels_per_pass({"coh_pairs": 0, "hex_variant": 0}, 0) == 4
